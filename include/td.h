@@ -1,0 +1,134 @@
+/*
+ * td.h -- C ABI of libtd, the GB300 (sm_103a) implementation of the block-level
+ * triangular-domain mapping g(lambda) of Navarro & Hitschfeld, "Improving the GPU space of
+ * computation under triangular domain problems" (arXiv:1308.1419), fused with the kernels
+ * it drives, plus the four strategies the paper compares it with.
+ *
+ * Common conventions
+ *   - T(m) = m(m+1)/2.  A lower triangle of side N *with* its diagonal is stored packed,
+ *     row-major: element (i, j), 0 <= j <= i < N, lives at offset T(i) + j (Sec. II-A,
+ *     Eq. (matrix_indexing) numbers blocks the same way).
+ *   - Device pointers are plain CUDA device addresses owned by the caller; every buffer the
+ *     library writes must be 16-byte aligned.  The library allocates no device memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is asynchronous
+ *     with respect to the host: it validates its arguments, enqueues its kernel(s) on
+ *     `stream` and returns.  Nothing synchronises.
+ *   - Errors: argument errors return TD_ERR_INVALID_ARG or TD_ERR_UNSUPPORTED before any
+ *     launch; a CUDA error at launch returns TD_ERR_CUDA.  td_last_error() gives the message
+ *     of the last failing call on the calling thread.  Nothing aborts or traps.
+ *   - rho is the side of a square block of the domain ("dimensional blocksize", Sec. II-A):
+ *     n = ceil(N / rho) blocks per side.
+ */
+#ifndef TD_H
+#define TD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TD_OK = 0,
+    TD_ERR_INVALID_ARG = 1,
+    TD_ERR_UNSUPPORTED = 2,
+    TD_ERR_CUDA = 3,
+    TD_ERR_TIMEOUT = 4
+} td_status;
+
+/* Mapping strategies (Sec. III-B): bounding box, upper-triangular mapping (Avril et al.),
+ * rectangular box (Jung et al.), recursive partition (Ries et al.), and the paper's
+ * lower-triangular mapping g(lambda) (Sec. II-A). */
+typedef enum {
+    TD_MAP_BB = 0,
+    TD_MAP_UTM = 1,
+    TD_MAP_RB = 2,
+    TD_MAP_REC = 3,
+    TD_MAP_LTM = 4
+} td_mapping;
+
+/* How the strategy's blocks are issued.  GRID: one CTA per block of the strategy's launch
+ * space, as in the paper.  PERSISTENT: a grid of (SM count x resident CTAs per SM) CTAs
+ * walks the same launch space with a grid-stride loop. */
+typedef enum {
+    TD_SCHED_GRID = 0,
+    TD_SCHED_PERSISTENT = 1
+} td_schedule;
+
+/* Launch-space accounting of one call (Sec. II-A: BB wastes n(n-1)/2 blocks, g(lambda)
+ * needs only n(n+1)/2).  `blocks` counts the strategy's blocks over all its launches,
+ * `useful_blocks` those holding at least one in-domain element, `wasted_blocks` the rest,
+ * `launches` the kernel launches, `ctas` the CTAs actually started (equal to `blocks`
+ * under TD_SCHED_GRID). */
+typedef struct {
+    uint64_t blocks;
+    uint64_t useful_blocks;
+    uint64_t wasted_blocks;
+    uint64_t launches;
+    uint64_t ctas;
+} td_launch_stats;
+
+/* ------------------------------------------------------------------ host-only helpers */
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int td_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  Owned by the library. */
+const char *td_last_error(void);
+
+/* T(N) = N(N+1)/2 if with_diag, else N(N-1)/2 (Sec. II-A). */
+uint64_t td_tri_size(uint32_t N, int with_diag);
+
+/* Words of the collision table for n spheres: T(ceil(n/32)) * 32 (see td_collide). */
+uint64_t td_collide_words(uint32_t n);
+
+/* Fills *stats with the launch space td_map_probe(m, sched, N, rho, ...) would use, without
+ * touching a GPU.  rho in {8, 16, 32}.  REC needs N to be a positive multiple of rho
+ * (Sec. III-B: N = m 2^k, m a multiple of rho; k is taken as large as possible), else
+ * TD_ERR_UNSUPPORTED. */
+td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_launch_stats *stats);
+
+/* ------------------------------------------------------------------ mapping kernels */
+
+/* Probe: the paper's dummy kernel (Sec. III-A, Sec. IV test (1)) made to write the whole
+ * domain.  Every in-domain thread of strategy m writes
+ *     out[T(i) + j] = splitmix32((uint32_t)(i * N + j)),   0 <= j <= i < N,
+ * where splitmix32(x) = fmix32(x + 0x9E3779B9) and fmix32 is the MurmurHash3 32-bit
+ * finaliser.  out: device, uint32[T(N)], 16-byte aligned.  rho in {8, 16, 32} (rho x rho
+ * threads per block; UTM uses rho^2-thread blocks over its thread index).  stats: host,
+ * may be NULL.  N = 0 is a no-op. */
+td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho,
+                       uint32_t *out, td_launch_stats *stats, void *stream);
+
+/* Coverage check of a strategy: every in-domain thread adds 1 to count[T(i) + j]
+ * (atomically).  A bijective mapping leaves every entry at exactly its previous value + 1.
+ * Same arguments and launch space as td_map_probe; count: device, uint32[T(N)]. */
+td_status td_map_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho,
+                       uint32_t *count, void *stream);
+
+/* Dump of a mapping function for unit indices u0 .. u0+count-1 into ij (device,
+ * uint32[2*count], pairs (i, j)):
+ *   TD_MAP_LTM: unit = block index lambda, (i, j) = g(lambda) of Eq. (theorem); N unused.
+ *   TD_MAP_UTM: unit = thread index k < T(N), (i, j) = the UTM pair of Sec. III-B for the
+ *               strict upper triangle of side N+1, rows reversed into the lower triangle:
+ *               i = N - a, j = b - a - 1.
+ *   TD_MAP_RB:  unit = y * W + x over the RB thread rectangle (W = N/2, H = N+1 for even N;
+ *               W = N/2 + 1, H = N for odd N).
+ * Other strategies: TD_ERR_UNSUPPORTED. */
+td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,
+                      void *stream);
+
+/* Exhaustive self-check of the fast g(lambda) (FP32 reciprocal square root plus an integer
+ * +-1 fix-up) over lambda in [lam0, lam0 + count), lam0 + count <= 2^48: counts the lambda
+ * whose (i, j) breaks T(i) <= lambda < T(i+1).  The fix-up is proven sufficient for
+ * lambda < 2^40; beyond that this call measures where it stops being enough.
+ * result: device, uint64[2], must hold {0, UINT64_MAX} on entry;
+ * on exit result[0] = number of failures, result[1] = smallest failing lambda. */
+td_status td_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TD_H */

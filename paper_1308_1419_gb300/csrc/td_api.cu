@@ -1,0 +1,249 @@
+// td_api.cu -- the C ABI of libtd (declared in include/td.h): argument validation, launch
+// planning and dispatch.  Nothing here allocates device memory or synchronises a stream.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+
+#include "td_device.cuh"
+#include "td_internal.h"
+
+namespace td {
+
+static thread_local char g_err[512] = "";
+
+td_status fail(td_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+td_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return TD_OK;
+    return fail(TD_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+td_status launch_status(const char *what) { return cuda_status(cudaGetLastError(), what); }
+
+int sm_count()
+{
+    static std::mutex mu;
+    static std::unordered_map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+    cache[dev] = n;
+    return n;
+}
+
+uint64_t persistent_ctas(const void *kernel, int threads, size_t smem, uint64_t units)
+{
+    static std::mutex mu;
+    static std::unordered_map<uint64_t, int> cache;  // key: device ^ kernel address ^ smem
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t key = reinterpret_cast<uint64_t>(kernel) ^ (uint64_t(dev) << 56) ^ (uint64_t(smem) << 40);
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) per_sm = it->second;
+    }
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm <= 0)
+            per_sm = 1;
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = per_sm;
+    }
+    const uint64_t g = uint64_t(per_sm) * uint64_t(sm_count());
+    if (units == 0) return 1;
+    return units < g ? units : g;
+}
+
+static int rec_levels(uint32_t N, uint32_t rho, uint32_t &m)
+{
+    if (rho == 0 || N == 0 || N % rho != 0) return -1;
+    int k = 0;
+    uint32_t mm = N;
+    while (mm % (2 * rho) == 0) {
+        mm /= 2;
+        ++k;
+    }
+    m = mm;
+    return k;
+}
+
+static const uint64_t kMaxGridX = 0x7fffffffull, kMaxGridY = 65535ull;
+
+td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, Plan &p)
+{
+    if (rho != 8 && rho != 16 && rho != 32) return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32 (got %u)", rho);
+    if (s != TD_SCHED_GRID && s != TD_SCHED_PERSISTENT) return fail(TD_ERR_INVALID_ARG, "unknown schedule %d", int(s));
+    const bool grid = s == TD_SCHED_GRID;
+    p = Plan{};
+    p.nb = (N + rho - 1) / rho;
+    const uint64_t nb = p.nb, per = uint64_t(rho) * rho;
+    p.launches = 1;
+    switch (m) {
+    case TD_MAP_BB:
+        p.blocks = nb * nb;
+        p.useful = tri(nb);
+        if (nb > kMaxGridY) return fail(TD_ERR_UNSUPPORTED, "BB needs ceil(N/rho) <= 65535");
+        break;
+    case TD_MAP_LTM:
+        p.blocks = p.useful = tri(nb);
+        if (grid && p.blocks > kMaxGridX) return fail(TD_ERR_UNSUPPORTED, "LTM grid launch needs T(n) < 2^31");
+        break;
+    case TD_MAP_UTM:
+        p.blocks = p.useful = (tri(N) + per - 1) / per;
+        if (grid && p.blocks > kMaxGridX) return fail(TD_ERR_UNSUPPORTED, "UTM grid launch needs T(N)/rho^2 < 2^31");
+        if (N >= (1u << 30)) return fail(TD_ERR_UNSUPPORTED, "UTM needs N < 2^30");
+        break;
+    case TD_MAP_RB: {
+        uint32_t W, H;
+        rb_dims(N, W, H);
+        const uint64_t gx = (W + rho - 1) / rho, gy = (uint64_t(H) + rho - 1) / rho;
+        p.blocks = p.useful = gx * gy;
+        if (grid && gy > kMaxGridY) return fail(TD_ERR_UNSUPPORTED, "RB grid launch needs ceil((N+1)/rho) <= 65535");
+        break;
+    }
+    case TD_MAP_REC: {
+        uint32_t mside = 0;
+        const int k = rec_levels(N, rho, mside);
+        if (k < 0) return fail(TD_ERR_UNSUPPORTED, "REC needs N = m 2^k with m a multiple of rho (N=%u, rho=%u)", N, rho);
+        p.rec_k = uint32_t(k);
+        p.rec_m = mside;
+        p.launches = uint64_t(k) + 1;
+        for (int l = 1; l <= k; ++l) {
+            const uint64_t sb = (N >> l) / rho, gx = N / (2 * rho);
+            p.blocks += gx * sb;
+            p.useful += gx * sb;
+            if (grid && sb > kMaxGridY) return fail(TD_ERR_UNSUPPORTED, "REC level grid exceeds 65535 rows");
+        }
+        const uint64_t mb = mside / rho;
+        p.blocks += (uint64_t(N) / rho) * mb;
+        p.useful += (uint64_t(1) << k) * tri(mb);
+        if (grid && mb > kMaxGridY) return fail(TD_ERR_UNSUPPORTED, "REC diagonal grid exceeds 65535 rows");
+        break;
+    }
+    default:
+        return fail(TD_ERR_INVALID_ARG, "unknown mapping %d", int(m));
+    }
+    return TD_OK;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static void fill_stats(td_launch_stats *st, const Plan &p, uint64_t ctas)
+{
+    if (!st) return;
+    st->blocks = p.blocks;
+    st->useful_blocks = p.useful;
+    st->wasted_blocks = p.blocks - p.useful;
+    st->launches = p.launches;
+    st->ctas = ctas;
+}
+
+}  // namespace td
+
+using namespace td;
+
+extern "C" {
+
+int td_version(void) { return 100; }
+
+const char *td_last_error(void) { return g_err; }
+
+uint64_t td_tri_size(uint32_t N, int with_diag)
+{
+    const uint64_t n = N;
+    return with_diag ? n * (n + 1) / 2 : n * (n ? n - 1 : 0) / 2;
+}
+
+uint64_t td_collide_words(uint32_t n)
+{
+    const uint64_t nt = (uint64_t(n) + 31) / 32;
+    return nt * (nt + 1) / 2 * 32;
+}
+
+td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_launch_stats *stats)
+{
+    g_err[0] = 0;
+    if (!stats) return fail(TD_ERR_INVALID_ARG, "stats is NULL");
+    Plan p;
+    const td_status st = plan_strategy(m, sched, N, rho, p);
+    if (st != TD_OK) return st;
+    fill_stats(stats, p, sched == TD_SCHED_GRID ? p.blocks : 0);
+    return TD_OK;
+}
+
+static td_status probe_or_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *out,
+                                td_launch_stats *stats, void *stream, bool cover)
+{
+    g_err[0] = 0;
+    Plan p;
+    td_status st = plan_strategy(m, sched, N, rho, p);
+    if (st != TD_OK) return st;
+    if (N == 0) {
+        fill_stats(stats, p, 0);
+        return TD_OK;
+    }
+    if (!out) return fail(TD_ERR_INVALID_ARG, "output pointer is NULL");
+    if (!aligned16(out)) return fail(TD_ERR_INVALID_ARG, "output pointer must be 16-byte aligned");
+    uint64_t ctas = 0;
+    st = launch_probe(m, sched, N, rho, out, cover, p, static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
+}
+
+td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *out,
+                       td_launch_stats *stats, void *stream)
+{
+    return probe_or_cover(m, sched, N, rho, out, stats, stream, false);
+}
+
+td_status td_map_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *count, void *stream)
+{
+    return probe_or_cover(m, sched, N, rho, count, nullptr, stream, true);
+}
+
+td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij, void *stream)
+{
+    g_err[0] = 0;
+    if (m != TD_MAP_LTM && m != TD_MAP_UTM && m != TD_MAP_RB)
+        return fail(TD_ERR_UNSUPPORTED, "td_map_dump supports LTM, UTM and RB");
+    if (count == 0) return TD_OK;
+    if (!ij) return fail(TD_ERR_INVALID_ARG, "ij is NULL");
+    if (!aligned16(ij)) return fail(TD_ERR_INVALID_ARG, "ij must be 16-byte aligned");
+    if (m == TD_MAP_LTM && u0 + count > (uint64_t(1) << 40))
+        return fail(TD_ERR_UNSUPPORTED, "LTM dump is exact for lambda < 2^40");
+    if (m == TD_MAP_UTM && (N >= (1u << 30) || u0 + count > tri(N)))
+        return fail(TD_ERR_INVALID_ARG, "UTM thread index must be < T(N)");
+    if (m == TD_MAP_RB) {
+        if (N == 0 || u0 + count > tri(N)) return fail(TD_ERR_INVALID_ARG, "RB unit must be < T(N)");
+    }
+    return launch_map_dump(m, N, u0, count, ij, static_cast<cudaStream_t>(stream));
+}
+
+td_status td_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, void *stream)
+{
+    g_err[0] = 0;
+    if (!result) return fail(TD_ERR_INVALID_ARG, "result is NULL");
+    if (!aligned16(result)) return fail(TD_ERR_INVALID_ARG, "result must be 16-byte aligned");
+    if (lam0 + count < lam0 || lam0 + count > (uint64_t(1) << 48))
+        return fail(TD_ERR_UNSUPPORTED, "td_ltm_check covers lambda < 2^48");
+    if (count == 0) return TD_OK;
+    return launch_ltm_check(lam0, count, result, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

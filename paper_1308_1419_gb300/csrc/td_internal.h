@@ -1,0 +1,40 @@
+// td_internal.h -- host-side declarations shared by the translation units of libtd.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "td.h"
+
+namespace td {
+
+// Records a formatted message for td_last_error() and returns `st`.
+td_status fail(td_status st, const char *fmt, ...);
+// Maps a CUDA error to TD_ERR_CUDA (recording `what`), or TD_OK.
+td_status cuda_status(cudaError_t e, const char *what);
+// Checks cudaGetLastError() after a launch.
+td_status launch_status(const char *what);
+
+// SM count of the current device (cached per device).
+int sm_count();
+// Persistent grid for a kernel: SM count x resident CTAs per SM (cached per device/kernel),
+// capped at `units` (at least 1).
+uint64_t persistent_ctas(const void *kernel, int threads, size_t smem, uint64_t units);
+
+// Launch space of a strategy (host closed forms; mirrors what the launchers issue).
+struct Plan {
+    uint64_t blocks = 0, useful = 0, launches = 0, ctas = 0;
+    uint32_t nb = 0;          // blocks per side, ceil(N / rho)
+    uint32_t rec_k = 0;       // REC levels
+    uint32_t rec_m = 0;       // REC diagonal triangle side
+};
+td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, Plan &p);
+
+// Launchers (stream-ordered, no synchronisation).
+td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
+                       bool cover, const Plan &p, cudaStream_t st, uint64_t *ctas);
+td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,
+                          cudaStream_t st);
+td_status launch_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st);
+
+}  // namespace td

@@ -1,0 +1,145 @@
+"""Thin Python binding of libtd (include/td.h).
+
+Argument marshalling only: every function has the name of the C entry point it calls,
+checks that tensors live on a CUDA device with the right dtype and size, passes raw device
+pointers and the current torch stream, and raises TDError on a non-zero status.  Torch only
+provides device memory and streams; all computation happens in libtd's kernels.  There is
+no fallback: if libtd.so is missing, importing this module fails.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libtd.so")
+if not os.path.exists(_PATH):
+    raise ImportError(f"{_PATH} is missing; build it first (python -m paper_1308_1419_gb300.build, "
+                      "needs nvcc with sm_103a support)")
+lib = C.CDLL(_PATH)
+
+MAPPINGS = {"BB": 0, "UTM": 1, "RB": 2, "REC": 3, "LTM": 4}
+SCHEDULES = {"grid": 0, "persistent": 1}
+STATUS = {0: "TD_OK", 1: "TD_ERR_INVALID_ARG", 2: "TD_ERR_UNSUPPORTED", 3: "TD_ERR_CUDA", 4: "TD_ERR_TIMEOUT"}
+
+
+class TDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class td_launch_stats(C.Structure):
+    _fields_ = [("blocks", C.c_uint64), ("useful_blocks", C.c_uint64), ("wasted_blocks", C.c_uint64),
+                ("launches", C.c_uint64), ("ctas", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+def _sig(name, res, *args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = list(args)
+    return f
+
+
+_vp, _u32, _u64, _int = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+_stats_p = C.POINTER(td_launch_stats)
+_c_version = _sig("td_version", _int)
+_c_last_error = _sig("td_last_error", C.c_char_p)
+_c_tri_size = _sig("td_tri_size", _u64, _u32, _int)
+_c_collide_words = _sig("td_collide_words", _u64, _u32)
+_c_plan = _sig("td_plan", _int, _int, _int, _u32, _u32, _stats_p)
+_c_map_probe = _sig("td_map_probe", _int, _int, _int, _u32, _u32, _vp, _stats_p, _vp)
+_c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
+_c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
+_c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
+
+
+def _check(status):
+    if status != 0:
+        raise TDError(status, _c_last_error().decode())
+
+
+def _mapping(m):
+    return MAPPINGS[m] if isinstance(m, str) else int(m)
+
+
+def _schedule(s):
+    return SCHEDULES[s] if isinstance(s, str) else int(s)
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t, dtype, numel, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() < numel:
+        raise ValueError(f"{name} needs at least {numel} elements, has {t.numel()}")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- host-only helpers
+
+def td_version() -> int:
+    return int(_c_version())
+
+
+def td_tri_size(N: int, with_diag: bool = True) -> int:
+    return int(_c_tri_size(N, int(bool(with_diag))))
+
+
+def td_collide_words(n: int) -> int:
+    return int(_c_collide_words(n))
+
+
+def td_plan(mapping, schedule, N: int, rho: int) -> dict:
+    st = td_launch_stats()
+    _check(_c_plan(_mapping(mapping), _schedule(schedule), N, rho, C.byref(st)))
+    return st.as_dict()
+
+
+# ---------------------------------------------------------------- mapping kernels
+
+def td_map_probe(mapping, schedule, N: int, rho: int, out: torch.Tensor = None, stream=None):
+    """Probe output (int32 tensor holding the uint32 bit patterns) and launch stats."""
+    total = td_tri_size(N)
+    if out is None:
+        out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
+    ptr = _dev(out, torch.int32, total, "out")
+    st = td_launch_stats()
+    _check(_c_map_probe(_mapping(mapping), _schedule(schedule), N, rho, ptr, C.byref(st), _stream(stream)))
+    return out, st.as_dict()
+
+
+def td_map_cover(mapping, schedule, N: int, rho: int, count: torch.Tensor = None, stream=None):
+    total = td_tri_size(N)
+    if count is None:
+        count = torch.zeros(max(total, 1), dtype=torch.int32, device="cuda")
+    ptr = _dev(count, torch.int32, total, "count")
+    _check(_c_map_cover(_mapping(mapping), _schedule(schedule), N, rho, ptr, _stream(stream)))
+    return count
+
+
+def td_map_dump(mapping, N: int, u0: int, count: int, ij: torch.Tensor = None, stream=None):
+    if ij is None:
+        ij = torch.empty(max(2 * count, 2), dtype=torch.int32, device="cuda")
+    ptr = _dev(ij, torch.int32, 2 * count, "ij")
+    _check(_c_map_dump(_mapping(mapping), N, u0, count, ptr, _stream(stream)))
+    return ij
+
+
+def td_ltm_check(lam0: int, count: int, result: torch.Tensor = None, stream=None):
+    if result is None:
+        result = torch.tensor([0, -1], dtype=torch.int64, device="cuda")
+    ptr = _dev(result, torch.int64, 2, "result")
+    _check(_c_ltm_check(lam0, count, ptr, _stream(stream)))
+    return result

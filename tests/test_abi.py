@@ -1,0 +1,89 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every entry point the
+header declares, and its host-only logic (sizes, launch planning, argument validation)
+agrees with the oracle's closed forms -- all without a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import oracle
+from paper_1308_1419_gb300.build import INCLUDE, build_libtd
+
+build_libtd()
+from paper_1308_1419_gb300 import td  # noqa: E402
+
+HEADER = os.path.join(INCLUDE, "td.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(td_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported():
+    names = _declared_functions()
+    assert "td_map_probe" in names and "td_last_error" in names
+    for name in names:
+        assert hasattr(td.lib, name), f"{name} declared in td.h but not exported"
+
+
+def test_sizes():
+    for N in [0, 1, 2, 3, 1000, 65536, 2**32 - 1]:
+        assert td.td_tri_size(N, True) == N * (N + 1) // 2
+        assert td.td_tri_size(N, False) == N * (N - 1) // 2 if N else td.td_tri_size(N, False) == 0
+    for n in [0, 1, 31, 32, 33, 32768, 100000]:
+        assert td.td_collide_words(n) == oracle.collide_words(n)
+
+
+@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB", "REC"])
+@pytest.mark.parametrize("N,rho", [(1, 8), (100, 8), (1024, 16), (1000, 8), (768, 16), (2048, 32)])
+def test_plan_matches_oracle_launch_space(strategy, N, rho):
+    if strategy == "REC" and N % rho:
+        with pytest.raises(td.TDError) as e:
+            td.td_plan(strategy, "grid", N, rho)
+        assert e.value.status == 2
+        return
+    _, ref = oracle.cover(strategy, N, rho)
+    got = td.td_plan(strategy, "grid", N, rho)
+    assert got["blocks"] == ref["launched"]
+    assert got["useful_blocks"] == ref["useful"]
+    assert got["wasted_blocks"] == ref["launched"] - ref["useful"]
+    assert got["launches"] == ref["launches"]
+    assert got["ctas"] == got["blocks"]
+
+
+def test_plan_paper_waste_counts():
+    # Sec. II-A: BB wastes n(n-1)/2 blocks; g(lambda) launches exactly n(n+1)/2 (none idle).
+    for N, rho in [(65536, 16), (30720, 16), (65536, 8)]:
+        n = -(-N // rho)
+        bb = td.td_plan("BB", "grid", N, rho)
+        lt = td.td_plan("LTM", "grid", N, rho)
+        assert bb["blocks"] == n * n and bb["wasted_blocks"] == n * (n - 1) // 2
+        assert lt["blocks"] == n * (n + 1) // 2 and lt["wasted_blocks"] == 0
+
+
+def test_argument_errors_return_before_launch():
+    st = td.td_launch_stats()
+    assert td._c_map_probe(4, 1, 1024, 7, 256, C.byref(st), None) == 1       # bad rho
+    assert "rho" in td._c_last_error().decode()
+    assert td._c_map_probe(4, 1, 1024, 16, None, C.byref(st), None) == 1     # NULL output
+    assert td._c_map_probe(4, 1, 1024, 16, 8, C.byref(st), None) == 1        # misaligned
+    assert td._c_map_probe(3, 1, 100, 8, 256, C.byref(st), None) == 2        # REC needs N % rho == 0
+    assert td._c_map_probe(9, 1, 100, 8, 256, C.byref(st), None) == 1        # unknown mapping
+    assert td._c_map_probe(4, 5, 100, 8, 256, C.byref(st), None) == 1        # unknown schedule
+    assert td._c_map_probe(4, 1, 0, 16, None, C.byref(st), None) == 0        # N = 0 is a no-op
+    assert td._c_map_dump(0, 100, 0, 10, 256, None) == 2                     # BB has no dump
+    assert td._c_ltm_check(0, 10, None, None) == 1
+    assert td._c_ltm_check(2**50, 10, 256, None) == 2
+
+
+def test_oracle_not_imported_by_product():
+    import glob
+    pkg = os.path.dirname(td.__file__)
+    for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True) + \
+            glob.glob(os.path.join(pkg, "csrc", "*")):
+        src = open(path, errors="ignore").read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
+        assert "td_oracle" not in src and "liboracle" not in src, path
