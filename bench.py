@@ -3,8 +3,8 @@
 
 Workload (the headline one): the mapping probe sweep.  One step = the g(lambda) probe over
 every triangle side N in {1024, 4096, 16384, 65536} and block side rho in {8, 16, 32} (12
-launches, persistent schedule); each in-domain thread writes uint32 splitmix32(i N + j) into
-packed lower-triangular storage.  The metric is useful triangle pairs per second.  The same
+launches, chunked schedule by default); each in-domain element gets uint32
+splitmix32(i N + j) in packed lower-triangular storage.  The metric is useful triangle pairs per second.  The same
 sweep is also timed for BB, UTM, RB and REC (both schedules) and reported under "compare"
 with the paper's improvement factor I = t_BB / t_strategy.
 
@@ -207,9 +207,9 @@ def run_ours(args):
                 per[key] = [e[key][0].elapsed_time(e[key][1]) for e in evs_all]
         return ms, launches, per
 
-    # ---- headline: g(lambda) sweep, persistent schedule
+    # ---- headline: g(lambda) sweep
     with ClockSampler(local) as clk:
-        ms, launches, per = timed("LTM", "persistent", args.steps, args.warmup, per_launch=True)
+        ms, launches, per = timed("LTM", args.sched, args.steps, args.warmup, per_launch=True)
     ms_t = torch.tensor([ms], device=dev)
     if dist is not None:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
@@ -220,7 +220,7 @@ def run_ours(args):
     # ---- compared strategies (same sweep), both schedules
     compare = {}
     for strategy in ([] if args.no_compare else STRATS):
-        for sched in ("persistent", "grid"):
+        for sched in (("chunked", "persistent", "grid") if strategy in ("LTM", "BB", "REC") else ("persistent", "grid")):
             cms, _, cper = timed(strategy, sched, max(3, args.steps // 2), 2, per_launch=True)
             compare[f"{strategy}/{sched}"] = {
                 "pairs_per_s": sweep_pairs() * max(3, args.steps // 2) / (cms / 1e3),
@@ -229,6 +229,21 @@ def run_ours(args):
     bb = compare["BB/grid"]["ms_N65536"] if compare else {}
     for key, c in compare.items():
         c["I_vs_BB_grid_N65536"] = {r: bb[r] / c["ms_N65536"][r] for r in bb}
+        same = compare.get("BB/" + key.split("/")[1])
+        if same:
+            c["I_vs_BB_same_schedule_N65536"] = {r: same["ms_N65536"][r] / c["ms_N65536"][r] for r in bb}
+
+    # ---- write-only reference: cudaMemsetAsync of the same 8.6 GB (not a roofline denominator)
+    for _ in range(3):
+        out.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        out.zero_()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    memset_gbps = 5 * out.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9
 
     # ---- roofline of the dominant kernel: g(lambda) probe launches at N = 65536
     peak, peak_kind = load_peaks()
@@ -239,7 +254,8 @@ def run_ours(args):
     dom = max(RHOS, key=lambda r: per_rho[r]["ms"])
     achieved = per_rho[dom]["GBps"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"k_ltm<rho={dom}, persistent> probe, N=65536",
+                "traffic": None, "kernel": f"g(lambda) probe, {args.sched} schedule, rho={dom}, N=65536",
+                "memset_write_GBps": memset_gbps,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs, copy)" if peak_kind == "measured" else "fallback",
                 "per_rho": {str(r): v for r, v in per_rho.items()},
                 "algorithmic_bytes_per_launch": 4 * tri(65536)}
@@ -252,7 +268,7 @@ def run_ours(args):
     def e2e_step():
         for N in SIZES:
             for rho in RHOS:
-                td.td_map_probe("LTM", "persistent", N, rho, out)
+                td.td_map_probe("LTM", args.sched, N, rho, out)
                 host[: tri(N)].copy_(out[: tri(N)], non_blocking=True)
     e2e = None
     if not args.no_e2e:
@@ -277,7 +293,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic (no input array; each pair writes a hash of (i, j))",
-            "config": {"workload": "probe sweep: N in {1024,4096,16384,65536} x rho in {8,16,32}, g(lambda) persistent",
+            "config": {"workload": f"probe sweep: N in {{1024,4096,16384,65536}} x rho in {{8,16,32}}, g(lambda), {args.sched}",
                        "useful_pairs_per_step": sweep_pairs(),
                        "l2": "outputs exceed L2 (8.6 GB per N=65536 launch)"},
             "gpu_launches": launches,
@@ -295,23 +311,49 @@ def run_case(args):
     """One kernel alone: W warm-up launches, then K timed launches (for profilers and sweeps)."""
     import torch
     from paper_1308_1419_gb300 import td
-    kind, strategy, sched, N, rho = args.case.split(":")
-    N, rho = int(N), int(rho)
-    assert kind == "probe"
-    out = torch.empty(tri(N), dtype=torch.int32, device="cuda")
+    from paper_1308_1419_gb300 import synth
+    parts = args.case.split(":")
+    kind, strategy, sched = parts[:3]
+    if kind == "probe":
+        N, rho = int(parts[3]), int(parts[4])
+        out = torch.empty(tri(N), dtype=torch.int32, device="cuda")
+        pairs, nbytes = tri(N), 4 * tri(N)
+        def call():
+            td.td_map_probe(strategy, sched, N, rho, out)
+    elif kind == "edm":
+        n, d, rho = int(parts[3]), int(parts[4]), int(parts[5])
+        if n == 16384 and d == 256:
+            xh = synth.clustered_points()
+        else:
+            xh = synth.uniform_points(n, d, synth.seed_for(1))
+        x = torch.from_numpy(xh).cuda()
+        out = torch.empty(tri(n), dtype=torch.float32, device="cuda")
+        pairs, nbytes = tri(n), 4 * tri(n)
+        def call():
+            td.td_edm(strategy, sched, x, rho, out)
+    elif kind == "collide":
+        n = int(parts[3])
+        c, r = synth.spheres(n)
+        ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+        table = torch.empty(td.td_collide_words(n), dtype=torch.int32, device="cuda")
+        pairs, nbytes = n * (n - 1) // 2, 4 * td.td_collide_words(n)
+        def call():
+            td.td_collide(strategy, sched, ct, rt, table)
+    else:
+        raise SystemExit(f"unknown case {args.case}")
     for _ in range(args.warmup):
-        td.td_map_probe(strategy, sched, N, rho, out)
+        call()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     for k in range(args.steps):
         ev[2 * k].record()
-        td.td_map_probe(strategy, sched, N, rho, out)
+        call()
         ev[2 * k + 1].record()
     torch.cuda.synchronize()
     ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
     med = statistics.median(ms)
     print(json.dumps({"case": args.case, "ms_median": med, "ms_min": min(ms),
-                      "pairs_per_s": tri(N) / (med / 1e3), "GBps": 4 * tri(N) / (med / 1e3) / 1e9}), flush=True)
+                      "pairs_per_s": pairs / (med / 1e3), "GBps_written": nbytes / (med / 1e3) / 1e9}), flush=True)
 
 
 def main():
@@ -323,8 +365,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-compare", action="store_true", help="skip the BB/UTM/RB/REC comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--sched", default="chunked", choices=["chunked", "persistent", "grid"],
+                    help="schedule of the headline g(lambda) sweep")
     ap.add_argument("--case", default="sweep",
-                    help="sweep (default) or probe:<strategy>:<sched>:<N>:<rho> to time one kernel alone")
+                    help="sweep (default), or one kernel alone: probe:<strategy>:<sched>:<N>:<rho>, "
+                         "edm:<strategy>:<sched>:<n>:<d>:<rho>, collide:<strategy>:<sched>:<n>")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

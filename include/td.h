@@ -48,12 +48,18 @@ typedef enum {
     TD_MAP_LTM = 4
 } td_mapping;
 
-/* How the strategy's blocks are issued.  GRID: one CTA per block of the strategy's launch
- * space, as in the paper.  PERSISTENT: a grid of (SM count x resident CTAs per SM) CTAs
- * walks the same launch space with a grid-stride loop. */
+/* How the strategy's blocks are issued.
+ *   GRID: one CTA per block of the strategy's launch space, one element per thread, as in
+ *     the paper.
+ *   PERSISTENT: a grid of (SM count x resident CTAs per SM) CTAs walks the same launch space
+ *     with a grid-stride loop, one element per thread.
+ *   CHUNKED (probe only; block strategies LTM, BB, REC): persistent warps walk the rows of the
+ *     strategy's blocks and write the packed output in aligned 16-byte chunks; a chunk belongs
+ *     to the block holding its first element, so each element is still written exactly once. */
 typedef enum {
     TD_SCHED_GRID = 0,
-    TD_SCHED_PERSISTENT = 1
+    TD_SCHED_PERSISTENT = 1,
+    TD_SCHED_CHUNKED = 2
 } td_schedule;
 
 /* Launch-space accounting of one call (Sec. II-A: BB wastes n(n-1)/2 blocks, g(lambda)
@@ -69,6 +75,14 @@ typedef struct {
     uint64_t ctas;
 } td_launch_stats;
 
+/* Library-wide options (process global; set them before launching work). */
+typedef enum {
+    /* 1 (default): the tiled distance-map kernels use the packed FP32 pair instructions
+     * (sub.rn.f32x2 / fma.rn.f32x2); 0: scalar FP32.  Both round identically. */
+    TD_OPT_EDM_F32X2 = 0,
+    TD_OPT_COUNT = 1
+} td_option;
+
 /* ------------------------------------------------------------------ host-only helpers */
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -77,14 +91,18 @@ int td_version(void);
 /* Message of the last failed call on this thread ("" if none).  Owned by the library. */
 const char *td_last_error(void);
 
+/* Sets / reads a library option.  Unknown option: TD_ERR_INVALID_ARG (td_get_option: 0). */
+td_status td_set_option(td_option opt, int value);
+int td_get_option(td_option opt);
+
 /* T(N) = N(N+1)/2 if with_diag, else N(N-1)/2 (Sec. II-A). */
 uint64_t td_tri_size(uint32_t N, int with_diag);
 
 /* Words of the collision table for n spheres: T(ceil(n/32)) * 32 (see td_collide). */
 uint64_t td_collide_words(uint32_t n);
 
-/* Fills *stats with the launch space td_map_probe(m, sched, N, rho, ...) would use, without
- * touching a GPU.  rho in {8, 16, 32}.  REC needs N to be a positive multiple of rho
+/* Fills *stats with the launch space td_map_probe / td_edm (m, sched, N, rho, ...) would use,
+ * without touching a GPU.  rho in {8, 16, 32, 64, 128}.  REC needs N to be a positive multiple of rho
  * (Sec. III-B: N = m 2^k, m a multiple of rho; k is taken as large as possible), else
  * TD_ERR_UNSUPPORTED. */
 td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_launch_stats *stats);
@@ -100,6 +118,35 @@ td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_
  * may be NULL.  N = 0 is a no-op. */
 td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho,
                        uint32_t *out, td_launch_stats *stats, void *stream);
+
+/* Euclidean distance map (Sec. IV): for every 0 <= j <= i < n,
+ *     out[T(i) + j] = sqrt(sum_{k<d} (x[i][k] - x[j][k])^2)     in FP32,
+ * evaluated as t = x[i][k] - x[j][k], s = fma(t, t, s) for k = 0 .. d-1 from s = 0, then a
+ * correctly rounded sqrt -- the same order in every kernel, so every strategy, schedule and
+ * rho gives bit-identical output.  x: device, float[n][d] row-major, 16-byte aligned;
+ * out: device, float[T(n)], 16-byte aligned.  d >= 1.
+ * rho in {8, 16, 32}: rho x rho threads per block, one element per thread, every strategy
+ *   (the paper's EDM kernel).
+ * rho in {64, 128}: one 256-thread CTA per rho x rho block with shared-memory coordinate
+ *   tiles and register tiles, for large d; TD_MAP_LTM, TD_MAP_BB and TD_MAP_REC only.
+ * stats: host, may be NULL.  n = 0 is a no-op. */
+td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho,
+                 float *out, td_launch_stats *stats, void *stream);
+
+/* Collision table (collision detection is a td-problem named in the abstract and Sec. I):
+ * spheres i > j collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, decided exactly.  The table is
+ * bit-packed in 32 x 32 bit-tiles over the tile triangle of side nt = ceil(n / 32): tile
+ * (bi, bj), bj <= bi, is tile number T(bi) + bj and owns words [32 (T(bi)+bj), +32); word r of
+ * it holds row i = 32 bi + r and its bit c (LSB first) holds column j = 32 bj + c.  Bits with
+ * i <= j, i >= n or j >= n are 0.  Every word of the table is written.
+ * m: TD_MAP_LTM (tiles issued by g(lambda)) or TD_MAP_BB (bounding box of tiles); sched: GRID
+ * or PERSISTENT.  One warp computes one tile.
+ * centers: device, int32[n][3], each coordinate in [-2^30, 2^30); radii: device, int32[n], each
+ * in [0, 16384] (inside these ranges the 32-bit evaluation equals the int64 definition;
+ * outside them results are unspecified but every access stays in bounds).  Both 4-byte
+ * aligned.  table: device, uint32[td_collide_words(n)], 16-byte aligned.  n = 0: no-op. */
+td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
+                     uint32_t *table, td_launch_stats *stats, void *stream);
 
 /* Coverage check of a strategy: every in-domain thread adds 1 to count[T(i) + j]
  * (atomically).  A bijective mapping leaves every entry at exactly its previous value + 1.

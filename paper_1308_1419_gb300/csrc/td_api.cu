@@ -87,8 +87,12 @@ static const uint64_t kMaxGridX = 0x7fffffffull, kMaxGridY = 65535ull;
 
 td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, Plan &p)
 {
-    if (rho != 8 && rho != 16 && rho != 32) return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32 (got %u)", rho);
-    if (s != TD_SCHED_GRID && s != TD_SCHED_PERSISTENT) return fail(TD_ERR_INVALID_ARG, "unknown schedule %d", int(s));
+    if (rho != 8 && rho != 16 && rho != 32 && rho != 64 && rho != 128)
+        return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16, 32, 64 or 128 (got %u)", rho);
+    if (s != TD_SCHED_GRID && s != TD_SCHED_PERSISTENT && s != TD_SCHED_CHUNKED)
+        return fail(TD_ERR_INVALID_ARG, "unknown schedule %d", int(s));
+    if (s == TD_SCHED_CHUNKED && m != TD_MAP_LTM && m != TD_MAP_BB && m != TD_MAP_REC)
+        return fail(TD_ERR_UNSUPPORTED, "the chunked schedule serves the block strategies LTM, BB and REC");
     const bool grid = s == TD_SCHED_GRID;
     p = Plan{};
     p.nb = (N + rho - 1) / rho;
@@ -142,6 +146,10 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
     return TD_OK;
 }
 
+static int g_options[TD_OPT_COUNT] = {1};
+
+int option(td_option opt) { return (opt >= 0 && opt < TD_OPT_COUNT) ? g_options[opt] : 0; }
+
 static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 static void fill_stats(td_launch_stats *st, const Plan &p, uint64_t ctas)
@@ -187,10 +195,21 @@ td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_
     return TD_OK;
 }
 
+td_status td_set_option(td_option opt, int value)
+{
+    g_err[0] = 0;
+    if (opt < 0 || opt >= TD_OPT_COUNT) return fail(TD_ERR_INVALID_ARG, "unknown option %d", int(opt));
+    g_options[opt] = value;
+    return TD_OK;
+}
+
+int td_get_option(td_option opt) { return option(opt); }
+
 static td_status probe_or_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *out,
                                 td_launch_stats *stats, void *stream, bool cover)
 {
     g_err[0] = 0;
+    if (rho > 32) return fail(TD_ERR_INVALID_ARG, "the probe needs rho 8, 16 or 32 (got %u)", rho);
     Plan p;
     td_status st = plan_strategy(m, sched, N, rho, p);
     if (st != TD_OK) return st;
@@ -215,6 +234,59 @@ td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho
 td_status td_map_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *count, void *stream)
 {
     return probe_or_cover(m, sched, N, rho, count, nullptr, stream, true);
+}
+
+td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
+                 td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    Plan p;
+    td_status st = plan_strategy(m, sched, n, rho, p);
+    if (st != TD_OK) return st;
+    if (rho > 32 && m != TD_MAP_LTM && m != TD_MAP_BB && m != TD_MAP_REC)
+        return fail(TD_ERR_UNSUPPORTED, "rho 64/128 (tiled EDM) supports LTM, BB and REC only");
+    if (d == 0) return fail(TD_ERR_INVALID_ARG, "d must be at least 1");
+    if (n == 0) {
+        fill_stats(stats, p, 0);
+        return TD_OK;
+    }
+    if (!x || !out) return fail(TD_ERR_INVALID_ARG, "x and out must be non-NULL");
+    if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
+    uint64_t ctas = 0;
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    st = rho <= 32 ? launch_edm_pair(m, sched, x, n, d, rho, out, p, cs, &ctas)
+                   : launch_edm_tiled(m, sched, x, n, d, rho, out, p, option(TD_OPT_EDM_F32X2) != 0, cs, &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
+}
+
+td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
+                     uint32_t *table, td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM and BB");
+    if (sched != TD_SCHED_GRID && sched != TD_SCHED_PERSISTENT)
+        return fail(TD_ERR_INVALID_ARG, "td_collide takes the GRID or PERSISTENT schedule");
+    const uint64_t nt = (uint64_t(n) + 31) / 32;
+    Plan p;
+    p.nb = static_cast<uint32_t>(nt);
+    p.blocks = m == TD_MAP_LTM ? tri(nt) : nt * nt;
+    p.useful = tri(nt);
+    p.launches = 1;
+    if (n == 0) {
+        fill_stats(stats, p, 0);
+        return TD_OK;
+    }
+    if (!centers || !radii || !table) return fail(TD_ERR_INVALID_ARG, "centers, radii and table must be non-NULL");
+    if (!aligned16(table)) return fail(TD_ERR_INVALID_ARG, "table must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(centers) | reinterpret_cast<uintptr_t>(radii)) & 3u)
+        return fail(TD_ERR_INVALID_ARG, "centers and radii must be 4-byte aligned");
+    if (sched == TD_SCHED_GRID && (p.blocks + 7) / 8 > kMaxGridX)
+        return fail(TD_ERR_UNSUPPORTED, "grid launch too large; use the persistent schedule");
+    uint64_t ctas = 0;
+    const td_status st = launch_collide(m, sched, centers, radii, n, table, static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
 }
 
 td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij, void *stream)

@@ -1,0 +1,101 @@
+// td_collide.cu -- pairwise collision table, one of the td-problems named in the abstract and
+// Sec. I of arXiv:1308.1419 (the UTM of Sec. III-B came from collision detection).
+//
+// Spheres i > j collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, decided exactly.  The strict lower
+// triangle is cut into 32 x 32 bit-tiles; tile (bi, bj), bj <= bi, is tile number T(bi) + bj of
+// the tile triangle and owns table words [32 (T(bi) + bj), 32 (T(bi) + bj) + 32): word r holds
+// row i = 32 bi + r, bit c (LSB first) column j = 32 bj + c.  One warp computes one tile:
+// lane c holds sphere j, the 32 row spheres sit in shared memory and are read by broadcast,
+// each row's 32 predicates become one word through __ballot_sync, and lane r keeps word r, so
+// the tile leaves in one coalesced 128-byte store.  Tiles are issued by g(lambda) over the
+// T(ceil(n/32)) tiles, or by BB over the bounding box of tiles.
+//
+// Exactness in 32-bit integers: with coordinates in [-2^30, 2^30) and radii in [0, 2^14],
+// R = r_i + r_j <= 2^15.  Each |delta| is clamped to R + 1 before squaring: if every |delta|
+// <= R the clamp changes nothing and the sum of squares is exact (< 3 (2^15)^2 < 2^32); if some
+// |delta| > R the clamped sum exceeds R^2, and so does the true one.  Either way the unsigned
+// 32-bit comparison equals the int64 definition.
+#include "td_device.cuh"
+#include "td_internal.h"
+#include "td_tiles.cuh"
+
+namespace td {
+namespace {
+
+constexpr int kWarps = 8;
+
+__device__ __forceinline__ uint32_t absdiff(int32_t a, int32_t b)
+{
+    const int32_t d = a - b;
+    return static_cast<uint32_t>(d < 0 ? -d : d);
+}
+
+template <class Tiles, bool P>
+__global__ void __launch_bounds__(32 * kWarps)
+    k_collide(Tiles tiles, const int32_t *__restrict__ c, const int32_t *__restrict__ rad, uint32_t n,
+              uint32_t *__restrict__ table)
+{
+    __shared__ int4 rows[kWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t first = uint64_t(blockIdx.x) * kWarps + warp;
+    const uint64_t stride = P ? uint64_t(gridDim.x) * kWarps : tiles.units;
+    for (uint64_t u = first; u < tiles.units; u += stride) {
+        uint32_t bi, bj;
+        if (!tiles(u, bi, bj)) continue;  // warp-uniform
+        const uint32_t j = 32 * bj + lane, ir = 32 * bi + lane;
+        int4 pj = make_int4(0, 0, 0, 0), pi = make_int4(0, 0, 0, 0);
+        if (j < n) pj = make_int4(__ldg(c + 3 * uint64_t(j)), __ldg(c + 3 * uint64_t(j) + 1), __ldg(c + 3 * uint64_t(j) + 2), __ldg(rad + j));
+        if (ir < n) pi = make_int4(__ldg(c + 3 * uint64_t(ir)), __ldg(c + 3 * uint64_t(ir) + 1), __ldg(c + 3 * uint64_t(ir) + 2), __ldg(rad + ir));
+        __syncwarp();
+        rows[warp][lane] = pi;
+        __syncwarp();
+        const bool diag = bi == bj;
+        const uint32_t rows_valid = n - 32 * bi >= 32 ? 32u : n - 32 * bi;  // rows of this tile below n
+        uint32_t word = 0;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            const int4 p = rows[warp][r];
+            const uint32_t R = static_cast<uint32_t>(p.w + pj.w), R1 = R + 1;
+            const uint32_t dx = min(absdiff(p.x, pj.x), R1);
+            const uint32_t dy = min(absdiff(p.y, pj.y), R1);
+            const uint32_t dz = min(absdiff(p.z, pj.z), R1);
+            const uint32_t s = dx * dx + dy * dy + dz * dz;
+            const bool hit = s <= R * R && j < n && uint32_t(r) < rows_valid && (!diag || lane < r);
+            const uint32_t b = __ballot_sync(0xffffffffu, hit);
+            if (lane == r) word = b;
+        }
+        const uint64_t t = tri(bi) + bj;
+        table[t * 32 + lane] = word;
+    }
+}
+
+template <class Tiles>
+td_status launch(const Tiles &t, bool P, const int32_t *c, const int32_t *r, uint32_t n, uint32_t *table,
+                 cudaStream_t st, uint64_t *ctas)
+{
+    const uint64_t need = (t.units + kWarps - 1) / kWarps;
+    if (P) {
+        auto k = k_collide<Tiles, true>;
+        const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, need);
+        k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, 0, st>>>(t, c, r, n, table);
+        *ctas += g;
+    } else {
+        k_collide<Tiles, false><<<dim3(static_cast<uint32_t>(need)), 32 * kWarps, 0, st>>>(t, c, r, n, table);
+        *ctas += need;
+    }
+    return launch_status("td_collide kernel");
+}
+
+}  // namespace
+
+td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
+                         uint32_t *table, cudaStream_t st, uint64_t *ctas)
+{
+    const bool P = s == TD_SCHED_PERSISTENT;
+    const uint32_t nt = (n + 31) / 32;
+    if (m == TD_MAP_LTM) return launch(tiles::Ltm{tri(nt)}, P, c, r, n, table, st, ctas);
+    if (m == TD_MAP_BB) return launch(tiles::Bb{uint64_t(nt) * nt, nt}, P, c, r, n, table, st, ctas);
+    return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM and BB");
+}
+
+}  // namespace td

@@ -33,6 +33,14 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
 // Launchers (stream-ordered, no synchronisation).
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
                        bool cover, const Plan &p, cudaStream_t st, uint64_t *ctas);
+td_status launch_edm_pair(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
+                          float *out, const Plan &p, cudaStream_t st, uint64_t *ctas);
+td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
+                           float *out, const Plan &p, bool x2, cudaStream_t st, uint64_t *ctas);
+td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
+                         uint32_t *table, cudaStream_t st, uint64_t *ctas);
+// Library options (td_set_option).
+int option(td_option opt);
 td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,
                           cudaStream_t st);
 td_status launch_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st);

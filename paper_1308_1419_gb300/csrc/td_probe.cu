@@ -1,15 +1,9 @@
-// td_probe.cu -- mapping kernels of the five strategies (Sec. II-A and III-B of
-// arXiv:1308.1419) driving the probe body (the paper's dummy kernel, Sec. III-A, made to write
-// every in-domain element) or the coverage body (one atomic increment per in-domain thread).
-//
-// Every kernel uses rho x rho threads per block (UTM: rho^2 threads over its thread index).
-// Every body call is guarded by 0 <= j <= i < N, so a mapping error can only show up as a
-// missed or doubled element, never as a store outside the triangle.
-// GRID schedule: one CTA per block of the strategy's launch space, as in the paper.
-// PERSISTENT schedule: (SMs x resident CTAs) CTAs walk the same launch space with a
-// grid-stride loop, so a wasted block costs one loop test instead of one CTA launch.
-#include "td_device.cuh"
-#include "td_internal.h"
+// td_probe.cu -- the five strategies' launch spaces (td_strategies.cuh) driving the probe body
+// (the paper's dummy kernel of Sec. III-A, made to write every in-domain element) or the
+// coverage body (one atomic increment per in-domain thread), plus the mapping dump and the
+// exhaustive self-check of g(lambda).
+#include "td_strategies.cuh"
+#include "td_tiles.cuh"
 
 namespace td {
 namespace {
@@ -31,242 +25,110 @@ struct CoverBody {
     }
 };
 
-// ---------------------------------------------------------------- LTM, Sec. II-A
-// Block lambda in [0, T(n)) -> (block row, block column) = g(lambda); diagonal blocks filter
-// their upper threads, edge blocks their threads beyond N.
-template <int RHO, bool P, class Body>
-__global__ void __launch_bounds__(RHO * RHO) k_ltm(uint32_t N, uint64_t units, Body body)
+// ---------------------------------------------------------------- chunked probe (block strategies)
+// Persistent warps walk the block rows of the launch space.  A row of a block -- element row
+// i, columns [bj rho, bj rho + L) -- is the flat range [s, s + L) of the packed output with
+// s = T(i) + bj rho.  The flat output is cut into aligned 4-element (16-byte) chunks, and
+// chunk c is written by the block whose row segment holds its first element 4c: the blocks
+// of every block strategy cover each element exactly once, so every chunk has exactly one
+// writer.  A chunk that runs past the segment continues in the same packed row (the next
+// block writes no chunk that starts before its own segment) or, at a row end, into the first
+// elements of the next row(s); the probe value is a function of (i, j) alone, so the writer
+// computes it wherever the element lies.
+//
+// Lanes: LPR lanes per block row, each taking CPL chunks (q, q + LPR, ...); a warp covers
+// RPG = 32 / LPR consecutive block rows, in (block, row) order, per group.
+template <int RHO, int CPL>
+struct ChunkGeom {
+    static constexpr int CPR = RHO / 4;          // chunks per full block row
+    static constexpr int LPR = CPR / CPL;        // lanes per block row
+    static constexpr int RPG = 32 / LPR;         // block rows per warp group
+    static_assert(LPR >= 1 && 32 % LPR == 0, "bad chunk geometry");
+};
+
+__device__ __forceinline__ uint4 probe4(uint32_t key)
 {
-    const uint32_t ty = threadIdx.x / RHO, tx = threadIdx.x % RHO;
-    const uint64_t stride = P ? gridDim.x : units;
-    for (uint64_t lam = blockIdx.x; lam < units; lam += stride) {
+    return make_uint4(splitmix32(key), splitmix32(key + 1), splitmix32(key + 2), splitmix32(key + 3));
+}
+
+template <class Tiles, int RHO, int CPL>
+__global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t *__restrict__ out)
+{
+    using G = ChunkGeom<RHO, CPL>;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    const uint64_t groups = (tiles.units * RHO + G::RPG - 1) / G::RPG;
+    const uint32_t q0 = lane % G::LPR;
+    for (uint64_t grp = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); grp < groups; grp += warps) {
+        const uint64_t R = grp * G::RPG + lane / G::LPR;  // global block-row index
+        const uint64_t u = R / RHO;
+        const uint32_t r = static_cast<uint32_t>(R % RHO);
         uint32_t bi, bj;
-        ltm_g(lam, bi, bj);
-        const uint32_t i = bi * RHO + ty, j = bj * RHO + tx;
-        if (j <= i && i < N) body(i, j);
-    }
-}
-
-// ---------------------------------------------------------------- BB, Sec. III-B
-// n x n grid; a block with B_x > B_y returns before computing any thread coordinate.
-template <int RHO, class Body>
-__global__ void __launch_bounds__(RHO * RHO) k_bb_grid(uint32_t N, Body body)
-{
-    const uint32_t bx = blockIdx.x, by = blockIdx.y;
-    if (bx > by) return;
-    const uint32_t i = by * RHO + threadIdx.x / RHO, j = bx * RHO + threadIdx.x % RHO;
-    if (j <= i && i < N) body(i, j);
-}
-
-template <int RHO, class Body>
-__global__ void __launch_bounds__(RHO * RHO) k_bb_persist(uint32_t N, uint32_t nb, Body body)
-{
-    const uint32_t ty = threadIdx.x / RHO, tx = threadIdx.x % RHO;
-    const uint32_t units = nb * nb;
-    for (uint32_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const uint32_t by = u / nb, bx = u - by * nb;
-        if (bx > by) continue;
-        const uint32_t i = by * RHO + ty, j = bx * RHO + tx;
-        if (j <= i && i < N) body(i, j);
-    }
-}
-
-// ---------------------------------------------------------------- UTM, Sec. III-B
-// Thread-level: thread index k = block * rho^2 + threadIdx < T(N).
-template <int RHO, bool P, class Body>
-__global__ void __launch_bounds__(RHO * RHO) k_utm(uint32_t N, uint64_t total, uint64_t nblk, Body body)
-{
-    const uint64_t stride = P ? gridDim.x : nblk;
-    for (uint64_t b = blockIdx.x; b < nblk; b += stride) {
-        const uint64_t k = b * (RHO * RHO) + threadIdx.x;
-        if (k < total) {
-            uint32_t i, j;
-            utm_map(k, N, i, j);
-            if (j <= i && i < N) body(i, j);
-        }
-    }
-}
-
-// ---------------------------------------------------------------- RB, Sec. III-B
-template <int RHO, class Body>
-__global__ void __launch_bounds__(RHO * RHO) k_rb_grid(uint32_t N, uint32_t W, uint32_t H, Body body)
-{
-    const uint32_t x = blockIdx.x * RHO + threadIdx.x % RHO;
-    const uint32_t y = blockIdx.y * RHO + threadIdx.x / RHO;
-    if (x < W && y < H) {
-        uint32_t i, j;
-        rb_map(N, x, y, i, j);
-        if (j <= i && i < N) body(i, j);
-    }
-}
-
-template <int RHO, class Body>
-__global__ void __launch_bounds__(RHO * RHO)
-    k_rb_persist(uint32_t N, uint32_t W, uint32_t H, uint32_t gx, uint64_t units, Body body)
-{
-    const uint32_t ty = threadIdx.x / RHO, tx = threadIdx.x % RHO;
-    for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
-        const uint32_t by = static_cast<uint32_t>(u / gx), bx = static_cast<uint32_t>(u - uint64_t(by) * gx);
-        const uint32_t x = bx * RHO + tx, y = by * RHO + ty;
-        if (x < W && y < H) {
-            uint32_t i, j;
-            rb_map(N, x, y, i, j);
-            if (j <= i && i < N) body(i, j);
-        }
-    }
-}
-
-// ---------------------------------------------------------------- REC, Sec. III-B
-// Level l (one launch): 2^(l-1) squares of side s = N / 2^l laid side by side along x;
-// square q covers rows [(2q+1)s, (2q+2)s) and columns [2qs, (2q+1)s).  gx = N/(2 rho)
-// blocks along x, s/rho along y.
-template <int RHO, bool P, class Body>
-__global__ void __launch_bounds__(RHO * RHO)
-    k_rec_level(uint32_t N, uint32_t s, uint32_t sb, uint32_t gx, uint64_t units, Body body)
-{
-    const uint32_t ty = threadIdx.x / RHO, tx = threadIdx.x % RHO;
-    const uint64_t stride = P ? gridDim.x : units;
-    for (uint64_t u = P ? blockIdx.x : 0; u < units; u += stride) {
-        uint32_t bx, by;
-        if (P) { by = static_cast<uint32_t>(u / gx); bx = static_cast<uint32_t>(u - uint64_t(by) * gx); }
-        else   { bx = blockIdx.x; by = blockIdx.y; }
-        const uint32_t q = bx / sb, cb = bx - q * sb;
-        const uint32_t i = (2 * q + 1) * s + by * RHO + ty;
-        const uint32_t j = 2 * q * s + cb * RHO + tx;
-        if (j <= i && i < N) body(i, j);
-    }
-}
-
-// Final pass: 2^k diagonal triangles of side m, each covered bounding-box style.
-template <int RHO, bool P, class Body>
-__global__ void __launch_bounds__(RHO * RHO)
-    k_rec_diag(uint32_t N, uint32_t m, uint32_t mb, uint32_t gx, uint64_t units, Body body)
-{
-    const uint32_t ty = threadIdx.x / RHO, tx = threadIdx.x % RHO;
-    const uint64_t stride = P ? gridDim.x : units;
-    for (uint64_t u = P ? blockIdx.x : 0; u < units; u += stride) {
-        uint32_t bx, by;
-        if (P) { by = static_cast<uint32_t>(u / gx); bx = static_cast<uint32_t>(u - uint64_t(by) * gx); }
-        else   { bx = blockIdx.x; by = blockIdx.y; }
-        const uint32_t t = bx / mb, lb = bx - t * mb;
-        if (lb > by) continue;
-        const uint32_t i = t * m + by * RHO + ty, j = t * m + lb * RHO + tx;
-        if (j <= i && i < N) body(i, j);
-    }
-}
-
-// ---------------------------------------------------------------- launchers
-
-template <class K>
-uint64_t grid_for(K kernel, bool P, int threads, uint64_t units)
-{
-    return P ? persistent_ctas(reinterpret_cast<const void *>(kernel), threads, 0, units) : units;
-}
-
-template <int RHO, class Body>
-td_status launch_rho(td_mapping m, bool P, uint32_t N, Body body, const Plan &p, cudaStream_t st,
-                     uint64_t *ctas)
-{
-    constexpr int threads = RHO * RHO;
-    switch (m) {
-    case TD_MAP_LTM: {
-        const uint64_t units = tri(p.nb);
-        if (P) {
-            auto k = k_ltm<RHO, true, Body>;
-            const uint64_t g = grid_for(k, true, threads, units);
-            k<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, units, body);
-            *ctas += g;
-        } else {
-            k_ltm<RHO, false, Body><<<dim3(static_cast<uint32_t>(units)), threads, 0, st>>>(N, units, body);
-            *ctas += units;
-        }
-        break;
-    }
-    case TD_MAP_BB: {
-        if (P) {
-            auto k = k_bb_persist<RHO, Body>;
-            const uint64_t g = grid_for(k, true, threads, uint64_t(p.nb) * p.nb);
-            k<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, p.nb, body);
-            *ctas += g;
-        } else {
-            k_bb_grid<RHO, Body><<<dim3(p.nb, p.nb), threads, 0, st>>>(N, body);
-            *ctas += uint64_t(p.nb) * p.nb;
-        }
-        break;
-    }
-    case TD_MAP_UTM: {
-        const uint64_t total = tri(N), nblk = (total + threads - 1) / threads;
-        if (P) {
-            auto k = k_utm<RHO, true, Body>;
-            const uint64_t g = grid_for(k, true, threads, nblk);
-            k<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, total, nblk, body);
-            *ctas += g;
-        } else {
-            k_utm<RHO, false, Body><<<dim3(static_cast<uint32_t>(nblk)), threads, 0, st>>>(N, total, nblk, body);
-            *ctas += nblk;
-        }
-        break;
-    }
-    case TD_MAP_RB: {
-        uint32_t W, H;
-        rb_dims(N, W, H);
-        const uint32_t gx = (W + RHO - 1) / RHO, gy = (H + RHO - 1) / RHO;
-        if (P) {
-            auto k = k_rb_persist<RHO, Body>;
-            const uint64_t units = uint64_t(gx) * gy;
-            const uint64_t g = grid_for(k, true, threads, units);
-            k<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, W, H, gx, units, body);
-            *ctas += g;
-        } else {
-            k_rb_grid<RHO, Body><<<dim3(gx, gy), threads, 0, st>>>(N, W, H, body);
-            *ctas += uint64_t(gx) * gy;
-        }
-        break;
-    }
-    case TD_MAP_REC: {
-        const uint32_t k = p.rec_k, mside = p.rec_m;
-        for (uint32_t l = 1; l <= k; ++l) {
-            const uint32_t s = N >> l, sb = s / RHO, gx = N / (2 * RHO);
-            const uint64_t units = uint64_t(gx) * sb;
-            if (P) {
-                auto kk = k_rec_level<RHO, true, Body>;
-                const uint64_t g = grid_for(kk, true, threads, units);
-                kk<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, s, sb, gx, units, body);
-                *ctas += g;
+        if (u >= tiles.units || !tiles(u, bi, bj)) continue;
+        const uint32_t i = bi * RHO + r;
+        if (i >= N) continue;
+        const uint32_t j0 = bj * RHO;
+        const uint32_t L = min(uint32_t(RHO), i - j0 + 1);
+        const uint64_t ti = tri(i);
+        const uint64_t s = ti + j0, end = s + L, rowend = ti + i;
+        const uint64_t first = (s + 3) & ~uint64_t(3);
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const uint64_t p = first + 4 * uint64_t(q0 + c * G::LPR);
+            if (p >= end) break;
+            if (p + 3 <= rowend) {
+                const uint32_t key = i * N + static_cast<uint32_t>(p - ti);
+                *reinterpret_cast<uint4 *>(out + p) = probe4(key);
             } else {
-                k_rec_level<RHO, false, Body><<<dim3(gx, sb), threads, 0, st>>>(N, s, sb, gx, 1, body);
-                *ctas += units;
+                uint32_t ii = i;
+                uint64_t tii = ti;
+                for (int k = 0; k < 4; ++k) {
+                    const uint64_t P = p + k;
+                    while (P > tii + ii) {  // past the end of row ii: continue in the next row
+                        tii += ii + 1;
+                        ++ii;
+                    }
+                    if (ii >= N) break;
+                    out[P] = splitmix32(ii * N + static_cast<uint32_t>(P - tii));
+                }
             }
         }
-        const uint32_t mb = mside / RHO, gx = N / RHO;
-        const uint64_t units = uint64_t(gx) * mb;
-        if (P) {
-            auto kk = k_rec_diag<RHO, true, Body>;
-            const uint64_t g = grid_for(kk, true, threads, units);
-            kk<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, mside, mb, gx, units, body);
-            *ctas += g;
-        } else {
-            k_rec_diag<RHO, false, Body><<<dim3(gx, mb), threads, 0, st>>>(N, mside, mb, gx, 1, body);
-            *ctas += units;
-        }
-        break;
     }
-    default:
-        return fail(TD_ERR_INVALID_ARG, "unknown mapping %d", int(m));
-    }
-    return launch_status("td probe/cover kernel");
 }
 
-template <class Body>
-td_status launch_body(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, Body body, const Plan &p,
-                      cudaStream_t st, uint64_t *ctas)
+template <class Tiles, int RHO>
+td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
 {
-    const bool P = s == TD_SCHED_PERSISTENT;
-    switch (rho) {
-    case 8: return launch_rho<8>(m, P, N, body, p, st, ctas);
-    case 16: return launch_rho<16>(m, P, N, body, p, st, ctas);
-    case 32: return launch_rho<32>(m, P, N, body, p, st, ctas);
-    default: return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32 (got %u)", rho);
+    constexpr int CPL = 2;
+    using G = ChunkGeom<RHO, CPL>;
+    if (t.units == 0) return TD_OK;
+    const uint64_t groups = (t.units * RHO + G::RPG - 1) / G::RPG;
+    auto k = k_probe_chunked<Tiles, RHO, CPL>;
+    const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (groups + 7) / 8);
+    k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, out);
+    *ctas += g;
+    return launch_status("td probe chunked kernel");
+}
+
+template <int RHO>
+td_status launch_chunked_rho(td_mapping m, uint32_t N, uint32_t *out, const Plan &p, cudaStream_t st, uint64_t *ctas)
+{
+    switch (m) {
+    case TD_MAP_LTM: return launch_chunked_tiles<tiles::Ltm, RHO>(tiles::Ltm{tri(p.nb)}, N, out, st, ctas);
+    case TD_MAP_BB:
+        return launch_chunked_tiles<tiles::Bb, RHO>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, N, out, st, ctas);
+    case TD_MAP_REC: {
+        for (uint32_t l = 1; l <= p.rec_k; ++l) {
+            const uint32_t sb = (N >> l) / RHO, gx = N / (2 * RHO);
+            const td_status s = launch_chunked_tiles<tiles::RecLevel, RHO>(tiles::RecLevel{uint64_t(gx) * sb, sb, gx},
+                                                                           N, out, st, ctas);
+            if (s != TD_OK) return s;
+        }
+        const uint32_t mb = p.rec_m / RHO, gx = N / RHO;
+        return launch_chunked_tiles<tiles::RecDiag, RHO>(tiles::RecDiag{uint64_t(gx) * mb, mb, gx}, N, out, st, ctas);
+    }
+    default:
+        return fail(TD_ERR_UNSUPPORTED, "the chunked schedule serves the block strategies LTM, BB and REC");
     }
 }
 
@@ -322,8 +184,17 @@ __global__ void k_ltm_check(uint64_t lam0, uint64_t count, unsigned long long *r
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out, bool cover,
                        const Plan &p, cudaStream_t st, uint64_t *ctas)
 {
-    if (cover) return launch_body(m, s, N, rho, CoverBody{out}, p, st, ctas);
-    return launch_body(m, s, N, rho, ProbeBody{out, N}, p, st, ctas);
+    if (s == TD_SCHED_CHUNKED) {
+        if (cover) return fail(TD_ERR_UNSUPPORTED, "coverage counting uses the GRID or PERSISTENT schedule");
+        switch (rho) {
+        case 8: return launch_chunked_rho<8>(m, N, out, p, st, ctas);
+        case 16: return launch_chunked_rho<16>(m, N, out, p, st, ctas);
+        case 32: return launch_chunked_rho<32>(m, N, out, p, st, ctas);
+        default: return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32");
+        }
+    }
+    if (cover) return strat::launch_body(m, s, N, rho, CoverBody{out}, p, st, ctas);
+    return strat::launch_body(m, s, N, rho, ProbeBody{out, N}, p, st, ctas);
 }
 
 td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij, cudaStream_t st)

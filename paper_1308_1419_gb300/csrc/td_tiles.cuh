@@ -1,0 +1,65 @@
+// td_tiles.cuh -- block-level launch spaces as "tile sources": a unit index u -> the block
+// (bi, bj), bj <= bi, that a CTA (or warp) processes, for the strategies whose unit is a whole
+// square block: g(lambda) (Sec. II-A), BB and REC (Sec. III-B).  Used by the kernels whose
+// block body needs the whole tile at once (shared-memory staging, warp ballots).
+#pragma once
+
+#include "td_device.cuh"
+
+namespace td {
+namespace tiles {
+
+// g(lambda): unit = block index lambda < T(nb).
+struct Ltm {
+    uint64_t units;
+    __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
+    {
+        ltm_g(u, bi, bj);
+        return true;
+    }
+};
+
+// BB: unit = by * nb + bx over the n x n bounding box; blocks above the diagonal are skipped.
+struct Bb {
+    uint64_t units;
+    uint32_t nb;
+    __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
+    {
+        const uint32_t by = static_cast<uint32_t>(u / nb), bx = static_cast<uint32_t>(u - uint64_t(by) * nb);
+        bi = by;
+        bj = bx;
+        return bx <= by;
+    }
+};
+
+// REC level: squares of sb x sb blocks laid along x (gx = N / (2 rho) blocks); square q covers
+// block rows [(2q+1) sb, (2q+2) sb) and block columns [2q sb, (2q+1) sb).
+struct RecLevel {
+    uint64_t units;
+    uint32_t sb, gx;
+    __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
+    {
+        const uint32_t by = static_cast<uint32_t>(u / gx), bx = static_cast<uint32_t>(u - uint64_t(by) * gx);
+        const uint32_t q = bx / sb, cb = bx - q * sb;
+        bi = (2 * q + 1) * sb + by;
+        bj = 2 * q * sb + cb;
+        return true;
+    }
+};
+
+// REC diagonal pass: 2^k triangles of mb x mb blocks, each covered bounding-box style.
+struct RecDiag {
+    uint64_t units;
+    uint32_t mb, gx;
+    __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
+    {
+        const uint32_t by = static_cast<uint32_t>(u / gx), bx = static_cast<uint32_t>(u - uint64_t(by) * gx);
+        const uint32_t t = bx / mb, lb = bx - t * mb;
+        bi = t * mb + by;
+        bj = t * mb + lb;
+        return lb <= by;
+    }
+};
+
+}  // namespace tiles
+}  // namespace td

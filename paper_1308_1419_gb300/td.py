@@ -18,7 +18,7 @@ if not os.path.exists(_PATH):
 lib = C.CDLL(_PATH)
 
 MAPPINGS = {"BB": 0, "UTM": 1, "RB": 2, "REC": 3, "LTM": 4}
-SCHEDULES = {"grid": 0, "persistent": 1}
+SCHEDULES = {"grid": 0, "persistent": 1, "chunked": 2}
 STATUS = {0: "TD_OK", 1: "TD_ERR_INVALID_ARG", 2: "TD_ERR_UNSUPPORTED", 3: "TD_ERR_CUDA", 4: "TD_ERR_TIMEOUT"}
 
 
@@ -51,6 +51,10 @@ _c_tri_size = _sig("td_tri_size", _u64, _u32, _int)
 _c_collide_words = _sig("td_collide_words", _u64, _u32)
 _c_plan = _sig("td_plan", _int, _int, _int, _u32, _u32, _stats_p)
 _c_map_probe = _sig("td_map_probe", _int, _int, _int, _u32, _u32, _vp, _stats_p, _vp)
+_c_edm = _sig("td_edm", _int, _int, _int, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
+_c_collide = _sig("td_collide", _int, _int, _int, _vp, _vp, _u32, _vp, _stats_p, _vp)
+_c_set_option = _sig("td_set_option", _int, _int, _int)
+_c_get_option = _sig("td_get_option", _int, _int)
 _c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
 _c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
 _c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
@@ -93,6 +97,17 @@ def td_version() -> int:
     return int(_c_version())
 
 
+OPTIONS = {"edm_f32x2": 0}
+
+
+def td_set_option(opt, value: int):
+    _check(_c_set_option(OPTIONS[opt] if isinstance(opt, str) else int(opt), int(value)))
+
+
+def td_get_option(opt) -> int:
+    return int(_c_get_option(OPTIONS[opt] if isinstance(opt, str) else int(opt)))
+
+
 def td_tri_size(N: int, with_diag: bool = True) -> int:
     return int(_c_tri_size(N, int(bool(with_diag))))
 
@@ -118,6 +133,36 @@ def td_map_probe(mapping, schedule, N: int, rho: int, out: torch.Tensor = None, 
     st = td_launch_stats()
     _check(_c_map_probe(_mapping(mapping), _schedule(schedule), N, rho, ptr, C.byref(st), _stream(stream)))
     return out, st.as_dict()
+
+
+def td_edm(mapping, schedule, x: torch.Tensor, rho: int, out: torch.Tensor = None, stream=None):
+    """Packed FP32 Euclidean distance map of the rows of x (n x d, float32) and launch stats."""
+    if x.dim() != 2:
+        raise ValueError("x must be a 2-D (n, d) tensor")
+    n, d = x.shape
+    xp = _dev(x, torch.float32, n * d, "x")
+    total = td_tri_size(n)
+    if out is None:
+        out = torch.empty(max(total, 1), dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, total, "out")
+    st = td_launch_stats()
+    _check(_c_edm(_mapping(mapping), _schedule(schedule), xp, n, d, rho, op, C.byref(st), _stream(stream)))
+    return out, st.as_dict()
+
+
+def td_collide(mapping, schedule, centers: torch.Tensor, radii: torch.Tensor, table: torch.Tensor = None,
+               stream=None):
+    """Bit-packed collision table (int32 tensor holding uint32 words) and launch stats."""
+    n = radii.numel()
+    cp = _dev(centers, torch.int32, 3 * n, "centers")
+    rp = _dev(radii, torch.int32, n, "radii")
+    words = td_collide_words(n)
+    if table is None:
+        table = torch.empty(max(words, 4), dtype=torch.int32, device=radii.device)
+    tp = _dev(table, torch.int32, words, "table")
+    st = td_launch_stats()
+    _check(_c_collide(_mapping(mapping), _schedule(schedule), cp, rp, n, tp, C.byref(st), _stream(stream)))
+    return table, st.as_dict()
 
 
 def td_map_cover(mapping, schedule, N: int, rho: int, count: torch.Tensor = None, stream=None):

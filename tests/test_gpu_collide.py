@@ -1,0 +1,76 @@
+"""GPU parity of the bit-packed collision table (a td-problem of the abstract and Sec. I):
+bit-exact against the oracle's int64 definition, for g(lambda) and BB tiles and both
+schedules."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_1419_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1308_1419_gb300 import td  # noqa: E402
+
+VARIANTS = [("LTM", "grid"), ("LTM", "persistent"), ("BB", "grid"), ("BB", "persistent")]
+
+
+def _table(c, r, mapping, sched):
+    ct = torch.from_numpy(np.ascontiguousarray(c, dtype=np.int32)).cuda()
+    rt = torch.from_numpy(np.ascontiguousarray(r, dtype=np.int32)).cuda()
+    words = td.td_collide_words(r.size)
+    table = torch.full((max(words, 4),), -1, dtype=torch.int32, device="cuda")
+    table, st = td.td_collide(mapping, sched, ct, rt, table)
+    return table[:words].cpu().numpy().view(np.uint32), st
+
+
+@pytest.mark.parametrize("mapping,sched", VARIANTS)
+def test_collide_benchmark_config_full_table(mapping, sched):
+    """n = 32768 spheres, centres U[0,2^20)^3, radii U[256,2048]: the whole table."""
+    c, r = synth.spheres()
+    got, st = _table(c, r, mapping, sched)
+    want = oracle.collide(c, r)
+    assert np.array_equal(got, want), int(np.count_nonzero(got != want))
+    assert st["useful_blocks"] == 1024 * 1025 // 2
+
+
+@pytest.mark.parametrize("mapping,sched", VARIANTS)
+def test_collide_dense_and_ragged(mapping, sched):
+    for n in [1, 2, 31, 32, 33, 63, 100, 1000, 4097]:
+        c, r = synth.spheres(n, seed=500 + n, coord_bits=12, rmin=0, rmax=600)
+        got, _ = _table(c, r, mapping, sched)
+        want = oracle.collide(c, r)
+        assert np.array_equal(got, want), (n, int(np.count_nonzero(got != want)))
+        assert want.any() or n < 2
+
+
+def test_collide_edge_cases():
+    n = 70
+    c = np.zeros((n, 3), dtype=np.int32)
+    r = np.zeros(n, dtype=np.int32)
+    got, _ = _table(c, r, "LTM", "persistent")
+    assert np.array_equal(got, oracle.collide(c, r))
+    assert sum(bin(int(w)).count("1") for w in got) == n * (n - 1) // 2
+    # exactly touching collides, one unit further does not; extreme allowed ranges
+    c = np.array([[0, 0, 0], [300, 400, 0], [0, 0, 0], [301, 400, 0],
+                  [-2**30, -2**30, -2**30], [2**30 - 1, 2**30 - 1, 2**30 - 1],
+                  [5, 5, 5], [5 + 16384 * 2, 5, 5]], dtype=np.int32)
+    r = np.array([200, 300, 200, 300, 16384, 16384, 16384, 16384], dtype=np.int32)
+    got, _ = _table(c, r, "LTM", "grid")
+    assert np.array_equal(got, oracle.collide(c, r))
+    w, b = oracle.collide_bitpos(1, 0)
+    assert (got[w] >> b) & 1 == 1
+    w, b = oracle.collide_bitpos(7, 6)
+    assert (got[w] >> b) & 1 == 1
+
+
+def test_collide_rejects():
+    c = torch.zeros(10, 3, dtype=torch.int32, device="cuda")
+    r = torch.zeros(10, dtype=torch.int32, device="cuda")
+    with pytest.raises(td.TDError):
+        td.td_collide("UTM", "grid", c, r)
+    with pytest.raises(td.TDError):
+        td.td_collide("LTM", "chunked", c, r)

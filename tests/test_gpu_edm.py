@@ -1,0 +1,136 @@
+"""GPU parity of the Euclidean distance map (Sec. IV, f(i,j) = sqrt(sum_k (a_i^k - a_j^k)^2))
+against the FP64 oracle: every kernel within 2e-6 relative, and -- since every kernel sums in
+the same order -- bit-identical across strategies, schedules, block sides and the packed
+f32x2 / scalar variants."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_1419_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1308_1419_gb300 import td  # noqa: E402
+
+RTOL = 2e-6        # stated agreement for the FP32 distance map
+STRATS = ["BB", "UTM", "RB", "REC", "LTM"]
+
+
+def _check_rel(got, want, ctx):
+    got = np.asarray(got, dtype=np.float64)
+    err = np.abs(got - want)
+    bad = err > RTOL * want + 1e-30
+    assert not bad.any(), (ctx, int(bad.sum()), float((err / np.maximum(want, 1e-30)).max()))
+
+
+def _edm(mapping, sched, x, rho):
+    out, st = td.td_edm(mapping, sched, x, rho)
+    return out.cpu().numpy()[: td.td_tri_size(x.shape[0])], st
+
+
+def _cases(mapping, rho, n):
+    if rho > 32 and mapping not in ("LTM", "BB", "REC"):
+        return False
+    if mapping == "REC" and n % rho:
+        return False
+    return True
+
+
+def test_plain_edm_config():
+    """n = 2048, d = 3, U[0,1)^3, rho = 16, BB and g(lambda): the plain-EDM workload."""
+    xh = synth.plain_edm()
+    want = oracle.edm(xh)
+    x = torch.from_numpy(xh).cuda()
+    ref = None
+    for mapping in STRATS:
+        for sched in ("grid", "persistent"):
+            got, st = _edm(mapping, sched, x, 16)
+            _check_rel(got, want, (mapping, sched))
+            if ref is None:
+                ref = got
+            assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (mapping, sched)
+    diag = np.array([oracle.tri(i) + i for i in range(2048)])
+    assert np.all(ref[diag] == 0.0)
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 16, 64])
+def test_edm_ragged_all_kernels(d):
+    for n in [1, 2, 17, 64, 100, 257, 640]:
+        xh = synth.uniform_points(n, d, 1000 + n + d)
+        want = oracle.edm(xh)
+        x = torch.from_numpy(xh).cuda()
+        ref = None
+        for rho in [8, 16, 32, 64, 128]:
+            for mapping in STRATS:
+                if not _cases(mapping, rho, n):
+                    continue
+                for sched in ("grid", "persistent"):
+                    got, _ = _edm(mapping, sched, x, rho)
+                    _check_rel(got, want, (n, d, rho, mapping, sched))
+                    if ref is None:
+                        ref = got
+                    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (n, d, rho, mapping, sched)
+
+
+def test_edm_f32x2_matches_scalar():
+    xh = synth.uniform_points(700, 64, 77)
+    x = torch.from_numpy(xh).cuda()
+    assert td.td_get_option("edm_f32x2") == 1
+    a, _ = _edm("LTM", "persistent", x, 128)
+    td.td_set_option("edm_f32x2", 0)
+    try:
+        b, _ = _edm("LTM", "persistent", x, 128)
+        c, _ = _edm("LTM", "persistent", x, 64)
+    finally:
+        td.td_set_option("edm_f32x2", 1)
+    assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
+    assert np.array_equal(a.view(np.uint32), c.view(np.uint32))
+
+
+def test_edm_precision_workload_fp32_direct_sampled():
+    """n = 16384, d = 256 Gaussian clusters (the precision workload) in FP32 direct form:
+    200k sampled pairs plus the diagonal against the FP64 oracle."""
+    xh = synth.clustered_points()
+    x = torch.from_numpy(xh).cuda()
+    out, _ = td.td_edm("LTM", "persistent", x, 128)
+    rng = np.random.default_rng(4)
+    ii = rng.integers(0, 16384, 200000).astype(np.uint32)
+    jj = (rng.random(200000) * (ii + 1)).astype(np.uint32)
+    pos = torch.from_numpy((ii.astype(np.int64) * (ii + 1) // 2 + jj).astype(np.int64)).cuda()
+    got = out[pos].cpu().numpy()
+    _check_rel(got, oracle.edm_pairs(xh, ii, jj), "n16384 d256")
+    diag = torch.arange(16384, device="cuda", dtype=torch.int64)
+    assert bool((out[diag * (diag + 1) // 2 + diag] == 0).all())
+    # the same map from the one-thread-per-element kernel is bit-identical
+    ref, _ = td.td_edm("LTM", "persistent", x, 16)
+    assert torch.equal(out, ref)
+
+
+def test_edm_large_n_sampled():
+    n, d = 32768, 3
+    xh = synth.uniform_points(n, d, 4242)
+    x = torch.from_numpy(xh).cuda()
+    out, _ = td.td_edm("LTM", "persistent", x, 16)
+    rng = np.random.default_rng(8)
+    ii = rng.integers(0, n, 300000).astype(np.uint32)
+    jj = (rng.random(300000) * (ii + 1)).astype(np.uint32)
+    pos = torch.from_numpy((ii.astype(np.int64) * (ii + 1) // 2 + jj)).cuda()
+    _check_rel(out[pos].cpu().numpy(), oracle.edm_pairs(xh, ii, jj), "n32768 d3")
+    # rows at the start and the end in full
+    for i0, i1 in [(0, 64), (n - 8, n)]:
+        a, b = oracle.tri(i0), oracle.tri(i1)
+        _check_rel(out[a:b].cpu().numpy(), oracle.edm(xh, i0, i1), (i0, i1))
+
+
+def test_edm_errors():
+    x = torch.zeros(10, 3, device="cuda")
+    with pytest.raises(td.TDError):
+        td.td_edm("UTM", "grid", x, 64)          # tiled kernels serve block strategies only
+    with pytest.raises(td.TDError):
+        td.td_edm("LTM", "grid", x, 12)          # unsupported rho
+    with pytest.raises(td.TDError):
+        td.td_edm("REC", "grid", x, 8)           # 10 is not a multiple of 8

@@ -31,7 +31,9 @@ def _u32(t):
     return t.cpu().numpy().view(np.uint32)
 
 
-def _supported(strategy, N, rho):
+def _supported(strategy, N, rho, sched="grid"):
+    if sched == "chunked" and strategy not in ("LTM", "BB", "REC"):
+        return False
     return not (strategy == "REC" and (N == 0 or N % rho))
 
 
@@ -41,11 +43,15 @@ def _first_diff(a, b):
 
 
 @pytest.mark.parametrize("strategy", STRATS)
-@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("sched", SCHEDS + ["chunked"])
 @pytest.mark.parametrize("rho", [8, 16, 32])
 def test_probe_matches_oracle_small(strategy, sched, rho):
-    for N in [1, 2, 7, 8, 33, 100, 255, 256, 1000, 1024, 3000, 4096]:
-        if not _supported(strategy, N, rho):
+    if not _supported(strategy, 1024, rho, sched):
+        with pytest.raises(td.TDError):
+            td.td_map_probe(strategy, sched, 1024, rho)
+        return
+    for N in [1, 2, 3, 4, 5, 7, 8, 33, 100, 255, 256, 1000, 1024, 3000, 4096]:
+        if not _supported(strategy, N, rho, sched):
             continue
         out = torch.full((td.td_tri_size(N),), SENTINEL, dtype=torch.int32, device="cuda")
         _, st = td.td_map_probe(strategy, sched, N, rho, out)
@@ -69,11 +75,12 @@ def test_cover_exactly_once_small(strategy, sched):
             assert c.size == td.td_tri_size(N) and np.all(c == 1), (strategy, sched, rho, N)
 
 
-def test_probe_full_size_ltm_against_oracle():
+@pytest.mark.parametrize("sched", ["persistent", "chunked"])
+def test_probe_full_size_ltm_against_oracle(sched):
     """N = 65536, the largest probe size: the full triangle (8.6 GB) against the oracle."""
     N = 65536
     out = torch.full((td.td_tri_size(N),), SENTINEL, dtype=torch.int32, device="cuda")
-    td.td_map_probe("LTM", "persistent", N, 16, out)
+    td.td_map_probe("LTM", sched, N, 16, out)
     torch.cuda.synchronize()
     rows = 4096
     for i0 in range(0, N, rows):
@@ -98,7 +105,9 @@ def test_probe_full_size_all_strategies_identical(rho):
         assert np.array_equal(got, oracle.probe(N, i, i + 1)), i
     out = torch.empty_like(ref)
     for strategy in STRATS:
-        for sched in SCHEDS:
+        for sched in SCHEDS + ["chunked"]:
+            if not _supported(strategy, N, rho, sched):
+                continue
             out.fill_(SENTINEL)
             td.td_map_probe(strategy, sched, N, rho, out)
             assert torch.equal(out, ref), (strategy, sched, rho)
