@@ -339,6 +339,42 @@ def run_case(args):
         pairs, nbytes = n * (n - 1) // 2, 4 * td.td_collide_words(n)
         def call():
             td.td_collide(strategy, sched, ct, rt, table)
+    elif kind == "batched":
+        # batched:<how>:<rho>:<ctas_per_sm>, how = one (single persistent launch), graph (its graph
+        # replay), per (one td_edm launch per problem), tune (autotuned one launch)
+        how, rho, cps = strategy, int(sched), int(parts[3])
+        ns, ds, xh = synth.batched_problems()
+        x = torch.from_numpy(xh).cuda()
+        xs, os_ = td.batched_sizes(ns, ds)
+        out = torch.empty(os_, dtype=torch.float32, device="cuda")
+        ws = torch.empty(td.td_edm_batched_workspace(len(ns)), dtype=torch.uint8, device="cuda")
+        pairs, nbytes = os_, 4 * os_
+        if how == "tune":
+            (rho, cps), _ = td.td_edm_batched_autotune(ns, ds, x, out, ws)
+            print(json.dumps({"autotuned": {"rho": rho, "ctas_per_sm": cps}}), flush=True)
+        total = td.td_edm_batched_plan(ns, ds, rho, ws)
+        if how in ("one", "tune"):
+            def call():
+                td.td_edm_batched_run(len(ns), rho, total, x, out, ws, cps)
+        elif how == "graph":
+            td.td_edm_batched_run(len(ns), rho, total, x, out, ws, cps)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                td.td_edm_batched_run(len(ns), rho, total, x, out, ws, cps)
+            def call():
+                graph.replay()
+        else:
+            xo = [0]
+            oo = [0]
+            for n, d in zip(ns, ds):
+                xo.append(xo[-1] + int(n) * int(d))
+                oo.append(oo[-1] + int(n) * (int(n) + 1) // 2)
+            xs_l = [x[xo[p]: xo[p + 1]].view(int(ns[p]), int(ds[p])).clone() for p in range(len(ns))]
+            outs = [torch.empty(oo[p + 1] - oo[p], dtype=torch.float32, device="cuda") for p in range(len(ns))]
+            def call():
+                for p in range(len(ns)):
+                    td.td_edm("LTM", "persistent", xs_l[p], rho, outs[p])
     else:
         raise SystemExit(f"unknown case {args.case}")
     for _ in range(args.warmup):

@@ -148,6 +148,50 @@ td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, ui
 td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
                      uint32_t *table, td_launch_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------ batched distance maps */
+
+/* Launch configuration of the batched distance map: block side rho (64 or 128) and CTAs per
+ * SM of the persistent grid (0 = as many as fit). */
+typedef struct {
+    uint32_t rho;
+    uint32_t ctas_per_sm;
+} td_batched_config;
+
+/* Bytes of device workspace td_edm_batched* needs for nprob problems (plan: prefix sums of
+ * the block counts and per-problem offsets). */
+size_t td_edm_batched_workspace(uint32_t nprob);
+
+/* Batched Euclidean distance maps: nprob independent problems, problem p with n[p] >= 1
+ * points of d[p] >= 1 features.  x_cat: device, the row-major n[p] x d[p] float blocks
+ * concatenated in problem order; out_cat: device, the packed triangles T(n[p]) concatenated in
+ * problem order (each exactly as td_edm would write it -- bit-identical).  All blocks of all
+ * problems form one launch space (problem p owns [P[p], P[p] + T(ceil(n[p]/rho))), P the
+ * prefix sum, problems laid heaviest first); one persistent launch walks it, finding each
+ * block's problem by binary search over P and its position by g(lambda) (Sec. II-A).
+ * n, d: host arrays.  ws: device workspace of td_edm_batched_workspace(nprob) bytes, 16-byte
+ * aligned (x_cat and out_cat too).  cfg: NULL = {64, 0}.  The plan upload uses a pageable
+ * host-to-device copy (it orders with `stream` but cannot be graph-captured); use
+ * td_edm_batched_plan + td_edm_batched_run to capture the launch. */
+td_status td_edm_batched(uint32_t nprob, const uint32_t *n, const uint32_t *d, const float *x_cat, float *out_cat,
+                         void *ws, size_t ws_bytes, const td_batched_config *cfg, td_launch_stats *stats,
+                         void *stream);
+
+/* Split form of td_edm_batched: _plan writes the plan for block side rho into ws and returns the
+ * launch-space size in *total_blocks (host); _run is a single kernel launch reading that plan
+ * (capturable in a CUDA graph; the plan must stay in ws). */
+td_status td_edm_batched_plan(uint32_t nprob, const uint32_t *n, const uint32_t *d, uint32_t rho, void *ws,
+                              size_t ws_bytes, uint64_t *total_blocks, void *stream);
+td_status td_edm_batched_run(uint32_t nprob, uint32_t rho, uint64_t total_blocks, const float *x_cat, float *out_cat,
+                             const void *ws, uint32_t ctas_per_sm, void *stream);
+
+/* Autotuner: times every rho in {64, 128} and CTAs-per-SM in {max, 1, 2, 3, 4} (one warm-up and
+ * three timed runs each, CUDA events on `stream`; synchronises), returns the fastest in *best and
+ * its time per run in *best_ms (host, may be NULL), and leaves ws planned for it.  out_cat is
+ * written (with the correct result). */
+td_status td_edm_batched_autotune(uint32_t nprob, const uint32_t *n, const uint32_t *d, const float *x_cat,
+                                  float *out_cat, void *ws, size_t ws_bytes, td_batched_config *best, float *best_ms,
+                                  void *stream);
+
 /* Coverage check of a strategy: every in-domain thread adds 1 to count[T(i) + j]
  * (atomically).  A bijective mapping leaves every entry at exactly its previous value + 1.
  * Same arguments and launch space as td_map_probe; count: device, uint32[T(N)]. */

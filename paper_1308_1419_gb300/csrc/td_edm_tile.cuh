@@ -1,0 +1,141 @@
+// td_edm_tile.cuh -- the register-tiled block body of the Euclidean distance map (Sec. IV of
+// arXiv:1308.1419), shared by td_edm (rho 64/128) and the batched distance map.
+//
+// One CTA of 256 threads computes one rho x rho block of the packed lower triangle.  The
+// block's rho row points and rho column points are staged in shared memory, KC features at a
+// time, feature-major; each thread keeps a TM x TM register tile (TM = rho / 16) for rows
+// {tr + 16 a} and columns {tc + 16 b}, so every feature step is two 128-bit shared loads and
+// TM^2 subtract/FMA pairs.  The shared-memory slot of row r is (r mod 16) TM + floor(r / 16):
+// the TM rows a thread owns sit side by side.  With X2, two columns go through each packed
+// sub.rn.f32x2 / fma.rn.f32x2 (sm_100+), which round every lane like the scalar instructions.
+//
+// Summation order is the one of every EDM kernel in libtd: t = x_i[k] - x_j[k],
+// s = fma(t, t, s) for k = 0 .. d-1 from s = 0, then sqrtf -- so the output is bit-identical to
+// the one-thread-per-element kernel.
+#pragma once
+
+#include "td_device.cuh"
+
+namespace td {
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long sub_f32x2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+template <int RHO, int KC, bool X2>
+struct EdmTile {
+    static constexpr int TM = RHO / 16;
+    static constexpr int LD = RHO + 4;  // padded row of a feature plane, keeps 16-byte alignment
+    static constexpr int SMEM_FLOATS = 2 * KC * LD;
+    static_assert(TM % 4 == 0, "TM must be a multiple of 4");
+
+    __device__ static __forceinline__ int slot(int r) { return (r & 15) * TM + (r >> 4); }
+
+    __device__ static void run(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
+                               float *__restrict__ out, float *sm)
+    {
+        const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+        float *sA = sm, *sB = sm + KC * LD;
+        const bool diag = i0 == j0;
+        float acc[TM][TM];
+        unsigned long long acc2[TM][TM / 2];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TM; ++b) acc[a][b] = 0.0f;
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TM / 2; ++b) acc2[a][b] = 0ull;
+
+        for (uint32_t k0 = 0; k0 < d; k0 += KC) {
+            const int kc = d - k0 < uint32_t(KC) ? int(d - k0) : KC;  // features in this chunk
+            for (int e = tid; e < RHO * kc; e += 256) {
+                const int r = e % RHO, kk = e / RHO;
+                const uint32_t k = k0 + kk;
+                const uint32_t i = i0 + r, j = j0 + r;
+                sA[kk * LD + slot(r)] = i < n ? __ldg(x + uint64_t(i) * d + k) : 0.0f;
+                if (!diag) sB[kk * LD + slot(r)] = j < n ? __ldg(x + uint64_t(j) * d + k) : 0.0f;
+            }
+            __syncthreads();
+            const float *B = diag ? sA : sB;
+#pragma unroll 2
+            for (int kk = 0; kk < kc; ++kk) {
+                float av[TM], bv[TM];
+#pragma unroll
+                for (int q = 0; q < TM; q += 4) {
+                    const float4 va = *reinterpret_cast<const float4 *>(sA + kk * LD + tr * TM + q);
+                    const float4 vb = *reinterpret_cast<const float4 *>(B + kk * LD + tc * TM + q);
+                    av[q] = va.x; av[q + 1] = va.y; av[q + 2] = va.z; av[q + 3] = va.w;
+                    bv[q] = vb.x; bv[q + 1] = vb.y; bv[q + 2] = vb.z; bv[q + 3] = vb.w;
+                }
+                if (X2) {
+                    unsigned long long b2[TM / 2];
+#pragma unroll
+                    for (int q = 0; q < TM / 2; ++q) b2[q] = pack2(bv[2 * q], bv[2 * q + 1]);
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) {
+                        const unsigned long long a2 = pack2(av[a], av[a]);
+#pragma unroll
+                        for (int q = 0; q < TM / 2; ++q) {
+                            const unsigned long long t = sub_f32x2(a2, b2[q]);
+                            acc2[a][q] = fma_f32x2(t, t, acc2[a][q]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < TM; ++a)
+#pragma unroll
+                        for (int b = 0; b < TM; ++b) {
+                            const float t = av[a] - bv[b];
+                            acc[a][b] = fmaf(t, t, acc[a][b]);
+                        }
+                }
+            }
+            __syncthreads();
+        }
+        if (X2) {
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int q = 0; q < TM / 2; ++q) unpack2(acc2[a][q], acc[a][2 * q], acc[a][2 * q + 1]);
+        }
+        // Thread (tr, tc) owns rows i0 + tr + 16a and columns j0 + tc + 16b; for fixed (a, b)
+        // a warp writes two 64-byte runs of two packed rows.
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+            const uint32_t i = i0 + tr + 16 * a;
+            if (i >= n) continue;
+            float *row = out + tri(i);
+#pragma unroll
+            for (int b = 0; b < TM; ++b) {
+                const uint32_t j = j0 + tc + 16 * b;
+                if (j <= i) row[j] = sqrtf(acc[a][b]);
+            }
+        }
+    }
+};
+
+}  // namespace td

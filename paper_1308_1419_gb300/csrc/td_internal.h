@@ -39,6 +39,7 @@ td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t
                            float *out, const Plan &p, bool x2, cudaStream_t st, uint64_t *ctas);
 td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
                          uint32_t *table, cudaStream_t st, uint64_t *ctas);
+size_t batched_workspace_bytes(uint32_t nprob);
 // Library options (td_set_option).
 int option(td_option opt);
 td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,

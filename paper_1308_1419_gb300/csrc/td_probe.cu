@@ -26,70 +26,60 @@ struct CoverBody {
 };
 
 // ---------------------------------------------------------------- chunked probe (block strategies)
-// Persistent warps walk the block rows of the launch space.  A row of a block -- element row
-// i, columns [bj rho, bj rho + L) -- is the flat range [s, s + L) of the packed output with
-// s = T(i) + bj rho.  The flat output is cut into aligned 4-element (16-byte) chunks, and
-// chunk c is written by the block whose row segment holds its first element 4c: the blocks
-// of every block strategy cover each element exactly once, so every chunk has exactly one
-// writer.  A chunk that runs past the segment continues in the same packed row (the next
-// block writes no chunk that starts before its own segment) or, at a row end, into the first
-// elements of the next row(s); the probe value is a function of (i, j) alone, so the writer
-// computes it wherever the element lies.
-//
-// Lanes: LPR lanes per block row, each taking CPL chunks (q, q + LPR, ...); a warp covers
-// RPG = 32 / LPR consecutive block rows, in (block, row) order, per group.
-template <int RHO, int CPL>
-struct ChunkGeom {
-    static constexpr int CPR = RHO / 4;          // chunks per full block row
-    static constexpr int LPR = CPR / CPL;        // lanes per block row
-    static constexpr int RPG = 32 / LPR;         // block rows per warp group
-    static_assert(LPR >= 1 && 32 % LPR == 0, "bad chunk geometry");
-};
-
+// Persistent warps walk the launch space in strips of S = 128 / rho consecutive units.  Units
+// that continue one block row -- blocks (bi, bj), (bi, bj+1), ... -- cover, in each element row
+// i of that block row, one contiguous flat range [s, e) of the packed output (s = T(i) + bj rho),
+// at most 128 elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
+// and chunk c is written by the block row range holding its first element 4c: the blocks of
+// every block strategy cover each element exactly once, so each chunk has exactly one writer.
+// All 32 lanes of a warp work on the same element row, lane l on chunk l of [s, e), so one
+// store instruction writes up to 512 contiguous bytes.  A chunk that runs past e continues in
+// the same packed row or, at a row end, into the first elements of the next row(s); the probe
+// value is a function of (i, j) alone, so the writer computes it wherever the element lies.
 __device__ __forceinline__ uint4 probe4(uint32_t key)
 {
     return make_uint4(splitmix32(key), splitmix32(key + 1), splitmix32(key + 2), splitmix32(key + 3));
 }
 
-template <class Tiles, int RHO, int CPL>
+template <class Tiles, int RHO>
 __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t *__restrict__ out)
 {
-    using G = ChunkGeom<RHO, CPL>;
+    constexpr uint32_t S = 128 / RHO;  // units per strip: up to 128 elements of a row
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-    const uint64_t groups = (tiles.units * RHO + G::RPG - 1) / G::RPG;
-    const uint32_t q0 = lane % G::LPR;
-    for (uint64_t grp = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); grp < groups; grp += warps) {
-        const uint64_t R = grp * G::RPG + lane / G::LPR;  // global block-row index
-        const uint64_t u = R / RHO;
-        const uint32_t r = static_cast<uint32_t>(R % RHO);
-        uint32_t bi, bj;
-        if (u >= tiles.units || !tiles(u, bi, bj)) continue;
-        const uint32_t i = bi * RHO + r;
-        if (i >= N) continue;
-        const uint32_t j0 = bj * RHO;
-        const uint32_t L = min(uint32_t(RHO), i - j0 + 1);
-        const uint64_t ti = tri(i);
-        const uint64_t s = ti + j0, end = s + L, rowend = ti + i;
-        const uint64_t first = (s + 3) & ~uint64_t(3);
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-            const uint64_t p = first + 4 * uint64_t(q0 + c * G::LPR);
-            if (p >= end) break;
-            if (p + 3 <= rowend) {
-                const uint32_t key = i * N + static_cast<uint32_t>(p - ti);
-                *reinterpret_cast<uint4 *>(out + p) = probe4(key);
-            } else {
-                uint32_t ii = i;
-                uint64_t tii = ti;
-                for (int k = 0; k < 4; ++k) {
-                    const uint64_t P = p + k;
-                    while (P > tii + ii) {  // past the end of row ii: continue in the next row
-                        tii += ii + 1;
-                        ++ii;
+    const uint64_t strips = (tiles.units + S - 1) / S;
+    for (uint64_t z = uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); z < strips; z += warps) {
+        const uint64_t uend = min(tiles.units, (z + 1) * S);
+        for (uint64_t u = z * S; u < uend;) {
+            uint32_t bi, bj;
+            const bool ok = tiles(u, bi, bj);
+            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(uend - u));
+            u += run;
+            if (!ok) continue;
+            const uint32_t jlo = bj * RHO;
+            for (uint32_t r = 0; r < uint32_t(RHO); ++r) {
+                const uint32_t i = bi * RHO + r;
+                if (i >= N) break;
+                const uint32_t jhi = min((bj + run) * RHO, i + 1);
+                const uint64_t ti = tri(i);
+                const uint64_t e = ti + jhi, rowend = ti + i;
+                const uint64_t p = ((ti + jlo + 3) & ~uint64_t(3)) + 4 * lane;
+                if (p >= e) continue;
+                if (p + 3 <= rowend) {
+                    const uint32_t key = i * N + static_cast<uint32_t>(p - ti);
+                    *reinterpret_cast<uint4 *>(out + p) = probe4(key);
+                } else {
+                    uint32_t ii = i;
+                    uint64_t tii = ti;
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t P = p + k;
+                        while (P > tii + ii) {  // past the end of row ii: continue in the next row
+                            tii += ii + 1;
+                            ++ii;
+                        }
+                        if (ii >= N) break;
+                        out[P] = splitmix32(ii * N + static_cast<uint32_t>(P - tii));
                     }
-                    if (ii >= N) break;
-                    out[P] = splitmix32(ii * N + static_cast<uint32_t>(P - tii));
                 }
             }
         }
@@ -99,12 +89,11 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
 template <class Tiles, int RHO>
 td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
 {
-    constexpr int CPL = 2;
-    using G = ChunkGeom<RHO, CPL>;
     if (t.units == 0) return TD_OK;
-    const uint64_t groups = (t.units * RHO + G::RPG - 1) / G::RPG;
-    auto k = k_probe_chunked<Tiles, RHO, CPL>;
-    const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (groups + 7) / 8);
+    constexpr uint32_t S = 128 / RHO;
+    const uint64_t strips = (t.units + S - 1) / S;
+    auto k = k_probe_chunked<Tiles, RHO>;
+    const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (strips + 7) / 8);
     k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, out);
     *ctas += g;
     return launch_status("td probe chunked kernel");

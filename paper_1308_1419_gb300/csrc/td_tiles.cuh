@@ -9,6 +9,10 @@
 namespace td {
 namespace tiles {
 
+// Each source also answers run(u, ok, bi, bj, cap): how many consecutive units from u (at most
+// cap) continue the same block row -- (bi, bj), (bi, bj+1), ... when unit u is a block (ok) --
+// or are consecutive wasted units (when it is not).
+
 // g(lambda): unit = block index lambda < T(nb).
 struct Ltm {
     uint64_t units;
@@ -16,6 +20,10 @@ struct Ltm {
     {
         ltm_g(u, bi, bj);
         return true;
+    }
+    __device__ __forceinline__ uint32_t run(uint64_t, bool, uint32_t bi, uint32_t bj, uint32_t cap) const
+    {
+        return min(cap, bi - bj + 1);  // the rest of block row bi
     }
 };
 
@@ -29,6 +37,10 @@ struct Bb {
         bi = by;
         bj = bx;
         return bx <= by;
+    }
+    __device__ __forceinline__ uint32_t run(uint64_t, bool ok, uint32_t bi, uint32_t bj, uint32_t cap) const
+    {
+        return ok ? min(cap, bi - bj + 1) : min(cap, nb - bj);  // to the diagonal / to the box edge
     }
 };
 
@@ -45,6 +57,11 @@ struct RecLevel {
         bj = 2 * q * sb + cb;
         return true;
     }
+    __device__ __forceinline__ uint32_t run(uint64_t u, bool, uint32_t, uint32_t, uint32_t cap) const
+    {
+        const uint32_t bx = static_cast<uint32_t>(u % gx);
+        return min(cap, sb - bx % sb);  // to the right edge of the square
+    }
 };
 
 // REC diagonal pass: 2^k triangles of mb x mb blocks, each covered bounding-box style.
@@ -58,6 +75,11 @@ struct RecDiag {
         bi = t * mb + by;
         bj = t * mb + lb;
         return lb <= by;
+    }
+    __device__ __forceinline__ uint32_t run(uint64_t u, bool ok, uint32_t bi, uint32_t bj, uint32_t cap) const
+    {
+        const uint32_t lb = static_cast<uint32_t>(u % gx) % mb;
+        return ok ? min(cap, bi - bj + 1) : min(cap, mb - lb);  // to the diagonal / to the triangle's edge
     }
 };
 

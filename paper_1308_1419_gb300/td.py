@@ -55,6 +55,18 @@ _c_edm = _sig("td_edm", _int, _int, _int, _vp, _u32, _u32, _u32, _vp, _stats_p, 
 _c_collide = _sig("td_collide", _int, _int, _int, _vp, _vp, _u32, _vp, _stats_p, _vp)
 _c_set_option = _sig("td_set_option", _int, _int, _int)
 _c_get_option = _sig("td_get_option", _int, _int)
+class td_batched_config(C.Structure):
+    _fields_ = [("rho", C.c_uint32), ("ctas_per_sm", C.c_uint32)]
+
+
+_c_batched_ws = _sig("td_edm_batched_workspace", C.c_size_t, _u32)
+_c_batched = _sig("td_edm_batched", _int, _u32, _vp, _vp, _vp, _vp, _vp, C.c_size_t,
+                  C.POINTER(td_batched_config), _stats_p, _vp)
+_c_batched_plan = _sig("td_edm_batched_plan", _int, _u32, _vp, _vp, _u32, _vp, C.c_size_t,
+                       C.POINTER(C.c_uint64), _vp)
+_c_batched_run = _sig("td_edm_batched_run", _int, _u32, _u32, _u64, _vp, _vp, _vp, _u32, _vp)
+_c_batched_tune = _sig("td_edm_batched_autotune", _int, _u32, _vp, _vp, _vp, _vp, _vp, C.c_size_t,
+                       C.POINTER(td_batched_config), C.POINTER(C.c_float), _vp)
 _c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
 _c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
 _c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
@@ -163,6 +175,76 @@ def td_collide(mapping, schedule, centers: torch.Tensor, radii: torch.Tensor, ta
     st = td_launch_stats()
     _check(_c_collide(_mapping(mapping), _schedule(schedule), cp, rp, n, tp, C.byref(st), _stream(stream)))
     return table, st.as_dict()
+
+
+def _host_u32(a, count, name):
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+    if arr.size != count:
+        raise ValueError(f"{name} must hold {count} values")
+    return arr, arr.ctypes.data_as(C.c_void_p)
+
+
+def td_edm_batched_workspace(nprob: int) -> int:
+    return int(_c_batched_ws(nprob))
+
+
+def batched_sizes(ns, ds):
+    """(x floats, out floats) of a batch: sum n_p d_p and sum T(n_p)."""
+    return (sum(int(n) * int(d) for n, d in zip(ns, ds)), sum(td_tri_size(int(n)) for n in ns))
+
+
+def td_edm_batched(ns, ds, x_cat: torch.Tensor, out_cat: torch.Tensor = None, ws: torch.Tensor = None,
+                   config=None, stream=None):
+    """All problems' packed distance maps in one persistent launch; returns (out_cat, ws, stats)."""
+    nprob = len(ns)
+    nh, npp = _host_u32(ns, nprob, "ns")
+    dh, dp = _host_u32(ds, nprob, "ds")
+    xs, os_ = batched_sizes(nh, dh)
+    xp = _dev(x_cat, torch.float32, xs, "x_cat")
+    if out_cat is None:
+        out_cat = torch.empty(max(os_, 4), dtype=torch.float32, device=x_cat.device)
+    op = _dev(out_cat, torch.float32, os_, "out_cat")
+    wsb = td_edm_batched_workspace(nprob)
+    if ws is None:
+        ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=x_cat.device)
+    wp = _dev(ws, torch.uint8, wsb, "ws")
+    cfg = None if config is None else C.byref(td_batched_config(*config))
+    st = td_launch_stats()
+    _check(_c_batched(nprob, npp, dp, xp, op, wp, ws.numel(), cfg, C.byref(st), _stream(stream)))
+    return out_cat, ws, st.as_dict()
+
+
+def td_edm_batched_plan(ns, ds, rho: int, ws: torch.Tensor, stream=None) -> int:
+    nprob = len(ns)
+    nh, npp = _host_u32(ns, nprob, "ns")
+    dh, dp = _host_u32(ds, nprob, "ds")
+    wp = _dev(ws, torch.uint8, td_edm_batched_workspace(nprob), "ws")
+    total = C.c_uint64()
+    _check(_c_batched_plan(nprob, npp, dp, rho, wp, ws.numel(), C.byref(total), _stream(stream)))
+    return int(total.value)
+
+
+def td_edm_batched_run(nprob: int, rho: int, total_blocks: int, x_cat: torch.Tensor, out_cat: torch.Tensor,
+                       ws: torch.Tensor, ctas_per_sm: int = 0, stream=None):
+    _check(_c_batched_run(nprob, rho, total_blocks, _dev(x_cat, torch.float32, 1, "x_cat"),
+                          _dev(out_cat, torch.float32, 1, "out_cat"), _dev(ws, torch.uint8, 1, "ws"),
+                          ctas_per_sm, _stream(stream)))
+
+
+def td_edm_batched_autotune(ns, ds, x_cat: torch.Tensor, out_cat: torch.Tensor, ws: torch.Tensor, stream=None):
+    """Returns ((rho, ctas_per_sm), ms per run) of the fastest configuration."""
+    nprob = len(ns)
+    nh, npp = _host_u32(ns, nprob, "ns")
+    dh, dp = _host_u32(ds, nprob, "ds")
+    xs, os_ = batched_sizes(nh, dh)
+    best = td_batched_config()
+    ms = C.c_float()
+    _check(_c_batched_tune(nprob, npp, dp, _dev(x_cat, torch.float32, xs, "x_cat"),
+                           _dev(out_cat, torch.float32, os_, "out_cat"),
+                           _dev(ws, torch.uint8, td_edm_batched_workspace(nprob), "ws"), ws.numel(),
+                           C.byref(best), C.byref(ms), _stream(stream)))
+    return (int(best.rho), int(best.ctas_per_sm)), float(ms.value)
 
 
 def td_map_cover(mapping, schedule, N: int, rho: int, count: torch.Tensor = None, stream=None):
