@@ -13,7 +13,8 @@
  *   row-major: element (i, j), 0 <= j <= i < N, lives at offset T(i) + j.  The same numbering
  *   is the paper's block numbering: block lambda = T(i) + j.
  *
- * Arithmetic: integers are exact (uint64 / int64); real values are computed in double.
+ * Arithmetic: integers are exact (64-bit, or 128-bit where sums of squared int32 differences
+ * exceed 64 bits); real values are computed in double.
  * Every function is a direct statement of its definition; nothing is blocked, fused or
  * reordered.
  */
@@ -352,14 +353,19 @@ void or_edm_pairs(const float *x, uint32_t d, const uint32_t *ii, const uint32_t
 /* ---------------------------------------------------------------- collision table */
 
 /* Collision detection, a td-problem named in the abstract and Sec. I: spheres i and j
- * (i != j) collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, evaluated exactly in int64. */
+ * (i != j) collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, evaluated exactly.  With int32 inputs a
+ * coordinate difference reaches 2^32 and the sum of three squares 3 * 2^64, beyond int64, so
+ * the squares are summed in unsigned 128-bit integers. */
 int or_collides(const int32_t *c, const int32_t *r, uint32_t i, uint32_t j)
 {
-    int64_t dx = (int64_t)c[3 * (uint64_t)i] - c[3 * (uint64_t)j];
-    int64_t dy = (int64_t)c[3 * (uint64_t)i + 1] - c[3 * (uint64_t)j + 1];
-    int64_t dz = (int64_t)c[3 * (uint64_t)i + 2] - c[3 * (uint64_t)j + 2];
+    unsigned __int128 s = 0;
+    for (int k = 0; k < 3; ++k) {
+        int64_t dk = (int64_t)c[3 * (uint64_t)i + k] - c[3 * (uint64_t)j + k];
+        uint64_t ak = (uint64_t)(dk < 0 ? -dk : dk);
+        s += (unsigned __int128)ak * ak;
+    }
     int64_t R = (int64_t)r[i] + r[j];
-    return dx * dx + dy * dy + dz * dz <= R * R;
+    return s <= (unsigned __int128)(R < 0 ? -R : R) * (unsigned __int128)(R < 0 ? -R : R);
 }
 
 /* Bit position of strict-lower pair (i, j), j < i, in the packed table: the table is

@@ -339,6 +339,26 @@ def test_collide_edge_cases():
     assert oracle.collide_pairs(c, r, [1], [0]).tolist() == [1]
 
 
+def test_collide_exact_for_full_int32_range():
+    """The predicate stays exact where int64 squares would overflow: compared with Python
+    integers on pairs spanning the whole int32 range."""
+    rng = np.random.default_rng(12)
+    lo, hi = -2**31, 2**31 - 1
+    c = rng.integers(lo, hi + 1, (300, 3)).astype(np.int32)
+    c[0] = [lo, lo, lo]
+    c[1] = [hi, hi, hi]
+    r = rng.integers(0, 2**31, 300).astype(np.int32)
+    r[0], r[1] = 2**31 - 1, 2**31 - 1
+    ii, jj = np.tril_indices(300, -1)
+    got = oracle.collide_pairs(c, r, ii, jj)
+    cc = [[int(v) for v in row] for row in c]
+    rr = [int(v) for v in r]
+    want = [int(sum((cc[i][k] - cc[j][k]) ** 2 for k in range(3)) <= (rr[i] + rr[j]) ** 2)
+            for i, j in zip(ii.tolist(), jj.tolist())]
+    assert got.tolist() == want
+    assert got[0] == 0  # (1, 0): |d|^2 = 3 (2^32 - 1)^2 > (2^32 - 2)^2
+
+
 def test_collide_bitpos_layout():
     assert oracle.collide_bitpos(1, 0) == (1, 0)
     assert oracle.collide_bitpos(31, 30) == (31, 30)
