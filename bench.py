@@ -339,6 +339,16 @@ def run_case(args):
         pairs, nbytes = n * (n - 1) // 2, 4 * td.td_collide_words(n)
         def call():
             td.td_collide(strategy, sched, ct, rt, table)
+    elif kind == "gram":
+        # gram:<n>:<d>: BF16 tensor-core Gram form with FP32 direct recompute
+        n, d = int(strategy), int(sched)
+        xh = synth.clustered_points() if (n, d) == (16384, 256) else synth.uniform_points(n, d, synth.seed_for(4))
+        x = torch.from_numpy(xh).cuda()
+        out = torch.empty(tri(n), dtype=torch.float32, device="cuda")
+        ws = torch.empty(td.td_edm_gram_workspace(n, d) + 1024, dtype=torch.uint8, device="cuda")
+        pairs, nbytes = tri(n), 4 * tri(n)
+        def call():
+            td.td_edm_gram(x, out, ws)
     elif kind == "batched":
         # batched:<how>:<rho>:<ctas_per_sm>, how = one (single persistent launch), graph (its graph
         # replay), per (one td_edm launch per problem), tune (autotuned one launch)

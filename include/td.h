@@ -148,6 +148,29 @@ td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, ui
 td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
                      uint32_t *table, td_launch_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------ Gram-form distance map */
+
+/* Bytes of device workspace td_edm_gram needs: a status block, n FP32 squared norms and a BF16
+ * copy of the n x d points. */
+size_t td_edm_gram_workspace(uint32_t n, uint32_t d);
+
+/* Euclidean distance map in Gram form on the tensor cores: D(i,j)^2 = |x_i|^2 + |x_j|^2 -
+ * 2 <x_i, x_j>, the inner products from BF16 copies of the points accumulated in FP32
+ * (tcgen05.mma, 128 x 128 blocks issued by g(lambda) over the block triangle), the squared
+ * norms in FP32 from the FP32 points.  A pair whose D^2 falls below 1e-2 (|x_i|^2 + |x_j|^2)
+ * (the diagonal included) is recomputed in the direct FP32 form sum_k (x_i[k] - x_j[k])^2, since
+ * the Gram subtraction cancels there.  Other pairs carry the BF16 error of the inner product.
+ * Same output layout as td_edm.  x: device, float[n][d], d a multiple of 8 in [8, 256], 16-byte
+ * aligned; out: device, float[T(n)], 16-byte aligned; ws: device, td_edm_gram_workspace(n, d)
+ * bytes, 1024-byte aligned.  Asynchronous; the pipeline's waits are bounded, and a wait that
+ * runs out is reported by td_edm_gram_status. */
+td_status td_edm_gram(const float *x, uint32_t n, uint32_t d, float *out, void *ws, size_t ws_bytes, void *stream);
+
+/* Synchronises `stream` and reads the status block of the last td_edm_gram that used ws:
+ * TD_ERR_TIMEOUT if a pipeline wait ran out, else TD_OK; *fallback_pairs (host, may be NULL)
+ * gets the number of pairs recomputed in the direct form. */
+td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *stream);
+
 /* ------------------------------------------------------------------ batched distance maps */
 
 /* Launch configuration of the batched distance map: block side rho (64 or 128) and CTAs per

@@ -289,6 +289,34 @@ td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, co
     return st;
 }
 
+size_t td_edm_gram_workspace(uint32_t n, uint32_t d) { return gram_workspace_bytes(n, d); }
+
+td_status td_edm_gram(const float *x, uint32_t n, uint32_t d, float *out, void *ws, size_t ws_bytes, void *stream)
+{
+    g_err[0] = 0;
+    if (n == 0) return TD_OK;
+    if (d == 0 || d % 8 != 0 || d > 256)
+        return fail(TD_ERR_UNSUPPORTED, "td_edm_gram needs d a multiple of 8 in [8, 256] (got %u)", d);
+    if (!x || !out || !ws) return fail(TD_ERR_INVALID_ARG, "x, out and workspace must be non-NULL");
+    if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(ws) & 1023u) return fail(TD_ERR_INVALID_ARG, "workspace must be 1024-byte aligned");
+    if (ws_bytes < gram_workspace_bytes(n, d)) return fail(TD_ERR_INVALID_ARG, "workspace too small");
+    return launch_gram(x, n, d, out, ws, static_cast<cudaStream_t>(stream));
+}
+
+td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *stream)
+{
+    g_err[0] = 0;
+    if (!ws) return fail(TD_ERR_INVALID_ARG, "workspace is NULL");
+    uint32_t err = 0;
+    uint64_t fb = 0;
+    const td_status s = read_gram_status(ws, &err, &fb, static_cast<cudaStream_t>(stream));
+    if (s != TD_OK) return s;
+    if (fallback_pairs) *fallback_pairs = fb;
+    if (err != 0) return fail(TD_ERR_TIMEOUT, "td_edm_gram: a pipeline wait timed out (code %u)", err);
+    return TD_OK;
+}
+
 td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij, void *stream)
 {
     g_err[0] = 0;

@@ -40,6 +40,9 @@ td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t
 td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
                          uint32_t *table, cudaStream_t st, uint64_t *ctas);
 size_t batched_workspace_bytes(uint32_t nprob);
+size_t gram_workspace_bytes(uint32_t n, uint32_t d);
+td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *ws, cudaStream_t st);
+td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cudaStream_t st);
 // Library options (td_set_option).
 int option(td_option opt);
 td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,

@@ -26,25 +26,41 @@ struct CoverBody {
 };
 
 // ---------------------------------------------------------------- chunked probe (block strategies)
-// Persistent warps walk the launch space in strips of S = 128 / rho consecutive units.  Units
+// Persistent warps walk the launch space in strips of S = 256 / rho consecutive units.  Units
 // that continue one block row -- blocks (bi, bj), (bi, bj+1), ... -- cover, in each element row
 // i of that block row, one contiguous flat range [s, e) of the packed output (s = T(i) + bj rho),
-// at most 128 elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
+// at most 256 elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
 // and chunk c is written by the block row range holding its first element 4c: the blocks of
 // every block strategy cover each element exactly once, so each chunk has exactly one writer.
-// All 32 lanes of a warp work on the same element row, lane l on chunk l of [s, e), so one
-// store instruction writes up to 512 contiguous bytes.  A chunk that runs past e continues in
+// All 32 lanes of a warp work on the same element row, lane l on chunks l and l + 32 of [s, e),
+// so one store instruction writes up to 512 contiguous bytes.  A chunk that runs past e continues in
 // the same packed row or, at a row end, into the first elements of the next row(s); the probe
 // value is a function of (i, j) alone, so the writer computes it wherever the element lies.
+// splitmix32 with its right shifts taken as high halves of multiplications
+// (z >> s = umulhi(z, 2^(32-s))): the same function, but the shifts issue on the FMA pipe
+// instead of the integer ALU pipe, which the xors and the index arithmetic already load.
+__device__ __forceinline__ uint32_t xor_shr(uint32_t z, uint32_t pow2) { return z ^ __umulhi(z, pow2); }
+
+__device__ __forceinline__ uint32_t splitmix32_mulshift(uint32_t x)
+{
+    uint32_t z = x + 0x9E3779B9u;
+    z = xor_shr(z, 1u << 16) * 0x85EBCA6Bu;
+    z = xor_shr(z, 1u << 19) * 0xC2B2AE35u;
+    return xor_shr(z, 1u << 16);
+}
+
 __device__ __forceinline__ uint4 probe4(uint32_t key)
 {
-    return make_uint4(splitmix32(key), splitmix32(key + 1), splitmix32(key + 2), splitmix32(key + 3));
+    return make_uint4(splitmix32_mulshift(key), splitmix32_mulshift(key + 1), splitmix32_mulshift(key + 2),
+                      splitmix32_mulshift(key + 3));
 }
+
+constexpr uint32_t kStripElems = 256;  // elements of one packed row a strip covers (2 chunks per lane)
 
 template <class Tiles, int RHO>
 __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t *__restrict__ out)
 {
-    constexpr uint32_t S = 128 / RHO;  // units per strip: up to 128 elements of a row
+    constexpr uint32_t S = kStripElems / RHO;  // units per strip
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     const uint64_t strips = (tiles.units + S - 1) / S;
@@ -60,25 +76,29 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
             for (uint32_t r = 0; r < uint32_t(RHO); ++r) {
                 const uint32_t i = bi * RHO + r;
                 if (i >= N) break;
-                const uint32_t jhi = min((bj + run) * RHO, i + 1);
+                const uint32_t jhi = min((bj + run) * RHO, i + 1);  // row-local end (exclusive)
                 const uint64_t ti = tri(i);
-                const uint64_t e = ti + jhi, rowend = ti + i;
-                const uint64_t p = ((ti + jlo + 3) & ~uint64_t(3)) + 4 * lane;
-                if (p >= e) continue;
-                if (p + 3 <= rowend) {
-                    const uint32_t key = i * N + static_cast<uint32_t>(p - ti);
-                    *reinterpret_cast<uint4 *>(out + p) = probe4(key);
-                } else {
-                    uint32_t ii = i;
-                    uint64_t tii = ti;
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t P = p + k;
-                        while (P > tii + ii) {  // past the end of row ii: continue in the next row
-                            tii += ii + 1;
-                            ++ii;
+                uint32_t *row = out + ti;
+                // first row-local j >= jlo whose flat index T(i) + j is a multiple of 4
+                const uint32_t c0 = jlo + ((4u - ((static_cast<uint32_t>(ti) + jlo) & 3u)) & 3u);
+#pragma unroll
+                for (uint32_t c = 0; c < kStripElems / 128; ++c) {
+                    const uint32_t j = c0 + 4 * (lane + 32 * c);
+                    if (j >= jhi) break;
+                    if (j + 3 <= i) {
+                        *reinterpret_cast<uint4 *>(row + j) = probe4(i * N + j);
+                    } else {  // the chunk runs past the end of row i into the next row(s)
+                        uint32_t ii = i;
+                        uint64_t tii = ti;
+                        for (uint32_t k = 0; k < 4; ++k) {
+                            const uint64_t P = ti + j + k;
+                            while (P > tii + ii) {
+                                tii += ii + 1;
+                                ++ii;
+                            }
+                            if (ii >= N) break;
+                            out[P] = splitmix32_mulshift(ii * N + static_cast<uint32_t>(P - tii));
                         }
-                        if (ii >= N) break;
-                        out[P] = splitmix32(ii * N + static_cast<uint32_t>(P - tii));
                     }
                 }
             }
@@ -90,7 +110,7 @@ template <class Tiles, int RHO>
 td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
 {
     if (t.units == 0) return TD_OK;
-    constexpr uint32_t S = 128 / RHO;
+    constexpr uint32_t S = kStripElems / RHO;
     const uint64_t strips = (t.units + S - 1) / S;
     auto k = k_probe_chunked<Tiles, RHO>;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (strips + 7) / 8);

@@ -67,6 +67,9 @@ _c_batched_plan = _sig("td_edm_batched_plan", _int, _u32, _vp, _vp, _u32, _vp, C
 _c_batched_run = _sig("td_edm_batched_run", _int, _u32, _u32, _u64, _vp, _vp, _vp, _u32, _vp)
 _c_batched_tune = _sig("td_edm_batched_autotune", _int, _u32, _vp, _vp, _vp, _vp, _vp, C.c_size_t,
                        C.POINTER(td_batched_config), C.POINTER(C.c_float), _vp)
+_c_gram_ws = _sig("td_edm_gram_workspace", C.c_size_t, _u32, _u32)
+_c_gram = _sig("td_edm_gram", _int, _vp, _u32, _u32, _vp, _vp, C.c_size_t, _vp)
+_c_gram_status = _sig("td_edm_gram_status", _int, _vp, C.POINTER(C.c_uint64), _vp)
 _c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
 _c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
 _c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
@@ -245,6 +248,38 @@ def td_edm_batched_autotune(ns, ds, x_cat: torch.Tensor, out_cat: torch.Tensor, 
                            _dev(ws, torch.uint8, td_edm_batched_workspace(nprob), "ws"), ws.numel(),
                            C.byref(best), C.byref(ms), _stream(stream)))
     return (int(best.rho), int(best.ctas_per_sm)), float(ms.value)
+
+
+def td_edm_gram_workspace(n: int, d: int) -> int:
+    return int(_c_gram_ws(n, d))
+
+
+def td_edm_gram(x: torch.Tensor, out: torch.Tensor = None, ws: torch.Tensor = None, stream=None):
+    """Gram-form (BF16 tensor-core) packed distance map with FP32 direct recompute of
+    cancelling pairs; returns (out, ws)."""
+    n, d = x.shape
+    xp = _dev(x, torch.float32, n * d, "x")
+    total = td_tri_size(n)
+    if out is None:
+        out = torch.empty(max(total, 4), dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, total, "out")
+    wsb = td_edm_gram_workspace(n, d)
+    if ws is None:
+        ws = torch.empty(wsb + 1024, dtype=torch.uint8, device=x.device)
+    base = ws.data_ptr()
+    off = (-base) % 1024  # the workspace must be 1024-byte aligned
+    if ws.numel() - off < wsb:
+        raise ValueError("workspace too small")
+    _check(_c_gram(xp, n, d, op, base + off, ws.numel() - off, _stream(stream)))
+    return out, ws
+
+
+def td_edm_gram_status(ws: torch.Tensor, stream=None) -> int:
+    """Synchronises; returns the number of pairs recomputed in the direct form (raises on a timeout)."""
+    off = (-ws.data_ptr()) % 1024
+    fb = C.c_uint64()
+    _check(_c_gram_status(ws.data_ptr() + off, C.byref(fb), _stream(stream)))
+    return int(fb.value)
 
 
 def td_map_cover(mapping, schedule, N: int, rho: int, count: torch.Tensor = None, stream=None):
