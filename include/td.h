@@ -207,6 +207,24 @@ td_status td_edm_batched_plan(uint32_t nprob, const uint32_t *n, const uint32_t 
 td_status td_edm_batched_run(uint32_t nprob, uint32_t rho, uint64_t total_blocks, const float *x_cat, float *out_cat,
                              const void *ws, uint32_t ctas_per_sm, void *stream);
 
+/* Allocation-free form of td_edm_batched, for callers that cannot allocate device memory: code
+ * running while a CUDA graph is being captured, under a memory pool whose budget is already
+ * reserved, or in a loop where an allocation (and the synchronisation it may bring) is not
+ * allowed.  The paper has no counterpart; this is a packaging of td_edm_batched.
+ * Instead of a caller workspace, the launch plan lives in a fixed array of device memory inside
+ * the library, sized for at most 1024 problems (about 40 KB; every GPU that loads the library
+ * holds it until the process exits).  The call performs no cudaMalloc, cudaFree or other
+ * allocation, on the device or the host.  More than 1024 problems: TD_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture begins.  Every call
+ * rewrites the whole plan (nothing in the array needs clearing) and the array keeps the last
+ * call's plan.  All calls share the one array: calls whose work overlaps on the GPU (different
+ * streams) race on it, so issue them on one stream.  The plan upload is a pageable host-to-device
+ * copy, which orders with `stream` and returns once the host image has been read.
+ * Other arguments and the result are those of td_edm_batched (bit-identical output). */
+td_status td_edm_batched_noalloc(uint32_t nprob, const uint32_t *n, const uint32_t *d, const float *x_cat,
+                                 float *out_cat, const td_batched_config *cfg, td_launch_stats *stats, void *stream);
+
 /* Autotuner: times every rho in {64, 128} and CTAs-per-SM in {max, 1, 2, 3, 4} (one warm-up and
  * three timed runs each, CUDA events on `stream`; synchronises), returns the fastest in *best and
  * its time per run in *best_ms (host, may be NULL), and leaves ws planned for it.  out_cat is

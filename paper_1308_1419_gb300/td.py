@@ -70,6 +70,8 @@ _c_batched_tune = _sig("td_edm_batched_autotune", _int, _u32, _vp, _vp, _vp, _vp
 _c_gram_ws = _sig("td_edm_gram_workspace", C.c_size_t, _u32, _u32)
 _c_gram = _sig("td_edm_gram", _int, _vp, _u32, _u32, _vp, _vp, C.c_size_t, _vp)
 _c_gram_status = _sig("td_edm_gram_status", _int, _vp, C.POINTER(C.c_uint64), _vp)
+_c_batched_noalloc = _sig("td_edm_batched_noalloc", _int, _u32, _vp, _vp, _vp, _vp,
+                          C.POINTER(td_batched_config), _stats_p, _vp)
 _c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
 _c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
 _c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
@@ -216,6 +218,20 @@ def td_edm_batched(ns, ds, x_cat: torch.Tensor, out_cat: torch.Tensor = None, ws
     st = td_launch_stats()
     _check(_c_batched(nprob, npp, dp, xp, op, wp, ws.numel(), cfg, C.byref(st), _stream(stream)))
     return out_cat, ws, st.as_dict()
+
+
+def td_edm_batched_noalloc(ns, ds, x_cat: torch.Tensor, out_cat: torch.Tensor, config=None, stream=None):
+    """td_edm_batched without a workspace: the plan lives in the library's own fixed device
+    array (at most 1024 problems), so the call allocates nothing.  out_cat must be given."""
+    nprob = len(ns)
+    nh, npp = _host_u32(ns, nprob, "ns")
+    dh, dp = _host_u32(ds, nprob, "ds")
+    xs, os_ = batched_sizes(nh, dh)
+    cfg = None if config is None else C.byref(td_batched_config(*config))
+    st = td_launch_stats()
+    _check(_c_batched_noalloc(nprob, npp, dp, _dev(x_cat, torch.float32, xs, "x_cat"),
+                              _dev(out_cat, torch.float32, os_, "out_cat"), cfg, C.byref(st), _stream(stream)))
+    return out_cat, st.as_dict()
 
 
 def td_edm_batched_plan(ns, ds, rho: int, ws: torch.Tensor, stream=None) -> int:
