@@ -33,7 +33,8 @@ struct CoverBody {
 // and chunk c is written by the block row range holding its first element 4c: the blocks of
 // every block strategy cover each element exactly once, so each chunk has exactly one writer.
 // All 32 lanes of a warp work on the same element row, lane l on chunks l and l + 32 of [s, e),
-// so one store instruction writes up to 512 contiguous bytes.  A chunk that runs past e continues in
+// so one store instruction writes up to 512 contiguous bytes; the stores are streaming
+// (st.global.cs), since every line is written once and never read back by the kernel.  A chunk that runs past e continues in
 // the same packed row or, at a row end, into the first elements of the next row(s); the probe
 // value is a function of (i, j) alone, so the writer computes it wherever the element lies.
 // splitmix32 with its right shifts taken as high halves of multiplications
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
                     const uint32_t j = c0 + 4 * (lane + 32 * c);
                     if (j >= jhi) break;
                     if (j + 3 <= i) {
-                        *reinterpret_cast<uint4 *>(row + j) = probe4(i * N + j);
+                        __stcs(reinterpret_cast<uint4 *>(row + j), probe4(i * N + j));
                     } else {  // the chunk runs past the end of row i into the next row(s)
                         uint32_t ii = i;
                         uint64_t tii = ti;

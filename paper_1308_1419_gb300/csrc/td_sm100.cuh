@@ -59,6 +59,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
+// Orders this thread's generic-proxy shared-memory accesses before later async-proxy (TMA)
+// accesses of the same memory; needed before a TMA overwrites shared memory that threads wrote
+// or read with ordinary instructions.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ TMA
 // 2-D tiled tensor load into shared memory, completing `bytes` on the mbarrier.  x is the
 // innermost (contiguous) coordinate in elements; x * element size must be a multiple of 16.
