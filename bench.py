@@ -233,17 +233,20 @@ def run_ours(args):
         if same:
             c["I_vs_BB_same_schedule_N65536"] = {r: same["ms_N65536"][r] / c["ms_N65536"][r] for r in bb}
 
-    # ---- write-only reference: cudaMemsetAsync of the same 8.6 GB (not a roofline denominator)
-    for _ in range(3):
-        out.zero_()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(5):
-        out.zero_()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    memset_gbps = 5 * out.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9
+    # ---- write-only reference: cudaMemsetAsync of the same 8.6 GB (not a roofline denominator;
+    # skipped with --no-compare so that a profiler's launch list holds only the timed step's kernels)
+    memset_gbps = None
+    if not args.no_compare:
+        for _ in range(3):
+            out.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            out.zero_()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        memset_gbps = 5 * out.numel() * 4 / (e0.elapsed_time(e1) / 1e3) / 1e9
 
     # ---- roofline of the dominant kernel: g(lambda) probe launches at N = 65536
     peak, peak_kind = load_peaks()
@@ -260,27 +263,39 @@ def run_ours(args):
                 "per_rho": {str(r): v for r, v in per_rho.items()},
                 "algorithmic_bytes_per_launch": 4 * tri(65536)}
 
-    # ---- end to end: same sweep through the public API, output read back to pinned host memory
-    host = None if args.no_e2e else torch.empty(tri(max(SIZES)), dtype=torch.int32, pin_memory=True)
-    d2h = sum(4 * tri(N) for N in SIZES for _ in RHOS)
-    e2e_steps = max(2, args.steps // 4)
-
-    def e2e_step():
-        for N in SIZES:
-            for rho in RHOS:
-                td.td_map_probe("LTM", args.sched, N, rho, out)
-                host[: tri(N)].copy_(out[: tri(N)], non_blocking=True)
+    # ---- end to end: the same sweep through the public API with the output in HOST memory.
+    # Two ways: (copy) the kernel writes device memory and the result is copied to pinned host
+    # memory; (direct) the kernel writes the pinned host buffer itself over the host link.  The
+    # faster one is reported; both are kept in the line.
     e2e = None
     if not args.no_e2e:
-        e2e_step()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
-        torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        e2e = {"value": sweep_pairs() * e2e_steps * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
-               "d2h_bytes_per_step": d2h}
+        host = torch.empty(tri(max(SIZES)), dtype=torch.int32, pin_memory=True)
+        d2h = sum(4 * tri(N) for N in SIZES for _ in RHOS)
+        e2e_steps = max(2, args.steps // 4)
+
+        def e2e_copy():
+            for N in SIZES:
+                for rho in RHOS:
+                    td.td_map_probe("LTM", args.sched, N, rho, out)
+                    host[: tri(N)].copy_(out[: tri(N)], non_blocking=True)
+
+        def e2e_direct():
+            for N in SIZES:
+                for rho in RHOS:
+                    td.td_map_probe("LTM", args.sched, N, rho, host)
+
+        modes = {}
+        for name, fn in (("copy", e2e_copy), ("direct", e2e_direct)):
+            fn()
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                fn()
+            torch.cuda.synchronize()
+            modes[name] = sweep_pairs() * e2e_steps * ws / (time.perf_counter() - t0)
+        best = max(modes, key=modes.get)
+        e2e = {"value": modes[best], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
+               "mode": best, "modes": modes}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -321,7 +336,11 @@ def run_case(args):
         def call():
             td.td_map_probe(strategy, sched, N, rho, out)
     elif kind == "edm":
+        # edm:<strategy>:<sched>:<n>:<d>:<rho>[:x2]  (x2: the library option that turns the packed
+        # f32x2 arithmetic of the tiled kernel on; same results)
         n, d, rho = int(parts[3]), int(parts[4]), int(parts[5])
+        if len(parts) > 6 and parts[6] == "x2":
+            td.td_set_option("edm_f32x2", 1)
         if n == 16384 and d == 256:
             xh = synth.clustered_points()
         else:

@@ -77,8 +77,9 @@ typedef struct {
 
 /* Library-wide options (process global; set them before launching work). */
 typedef enum {
-    /* 1 (default): the tiled distance-map kernels use the packed FP32 pair instructions
-     * (sub.rn.f32x2 / fma.rn.f32x2); 0: scalar FP32.  Both round identically. */
+    /* 1: the tiled distance-map kernels use the packed FP32 pair instructions
+     * (sub.rn.f32x2 / fma.rn.f32x2); 0 (default): scalar FP32, measured no slower on GB300.
+     * Both round identically, so the output does not depend on it. */
     TD_OPT_EDM_F32X2 = 0,
     TD_OPT_COUNT = 1
 } td_option;
@@ -106,6 +107,15 @@ uint64_t td_collide_words(uint32_t n);
  * (Sec. III-B: N = m 2^k, m a multiple of rho; k is taken as large as possible), else
  * TD_ERR_UNSUPPORTED. */
 td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_launch_stats *stats);
+
+/* Host-only partition of a triangle of side N (block side rho) over G ranks: rank r gets the
+ * contiguous block rows [*br0, *br1) -- the g(lambda) blocks lambda in [T(*br0), T(*br1)) -- and
+ * with them the contiguous slice [*off0, *off1) of the packed output.  Boundaries are the first
+ * block rows holding at least ceil(k T(N) / G) elements, so slices are balanced to within one
+ * block row; the G slices are disjoint and cover [0, T(N)).  Every (i, j) output is
+ * independent, so sharded ranks need no exchange beyond, optionally, gathering the slices. */
+td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_t *br0, uint32_t *br1, uint64_t *off0,
+                       uint64_t *off1);
 
 /* ------------------------------------------------------------------ mapping kernels */
 

@@ -146,7 +146,7 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
     return TD_OK;
 }
 
-static int g_options[TD_OPT_COUNT] = {1};
+static int g_options[TD_OPT_COUNT] = {0};
 
 int option(td_option opt) { return (opt >= 0 && opt < TD_OPT_COUNT) ? g_options[opt] : 0; }
 
@@ -314,6 +314,35 @@ td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *str
     if (s != TD_OK) return s;
     if (fallback_pairs) *fallback_pairs = fb;
     if (err != 0) return fail(TD_ERR_TIMEOUT, "td_edm_gram: a pipeline wait timed out (code %u)", err);
+    return TD_OK;
+}
+
+td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_t *br0, uint32_t *br1, uint64_t *off0,
+                       uint64_t *off1)
+{
+    g_err[0] = 0;
+    if (rho == 0 || G == 0 || r >= G) return fail(TD_ERR_INVALID_ARG, "need rho >= 1 and rank < G");
+    if (!br0 || !br1 || !off0 || !off1) return fail(TD_ERR_INVALID_ARG, "output pointers must be non-NULL");
+    const uint64_t nb = (uint64_t(N) + rho - 1) / rho, total = tri(N);
+    // elements in block rows [0, b)
+    auto elems = [&](uint64_t b) { return tri(b * rho < N ? b * rho : N); };
+    // first block row b with elems(b) >= ceil(k total / G)
+    auto boundary = [&](uint64_t k) {
+        if (k >= G) return nb;
+        const uint64_t target = (k * total + G - 1) / G;
+        uint64_t lo = 0, hi = nb;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) / 2;
+            if (elems(mid) >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
+    };
+    const uint64_t b0 = boundary(r), b1 = boundary(uint64_t(r) + 1);
+    *br0 = static_cast<uint32_t>(b0);
+    *br1 = static_cast<uint32_t>(b1);
+    *off0 = elems(b0);
+    *off1 = elems(b1);
     return TD_OK;
 }
 

@@ -14,7 +14,19 @@
 // R = r_i + r_j <= 2^15.  Each |delta| is clamped to R + 1 before squaring: if every |delta|
 // <= R the clamp changes nothing and the sum of squares is exact (< 3 (2^15)^2 < 2^32); if some
 // |delta| > R the clamped sum exceeds R^2, and so does the true one.  Either way the unsigned
-// 32-bit comparison equals the int64 definition.
+// 32-bit comparison equals the exact definition.
+//
+// Fast path on the FP32 pipe (full rate, where the integer ALU runs at half rate): when every
+// coordinate of the tile's 64 spheres lies in (-2^23, 2^23), coordinate differences are integers
+// below 2^24 and exact in FP32.  The sum of squares s, formed with one multiply and two FMAs, is
+// then within a factor (1 +- 3u) of the truth (u = 2^-24), and R^2 (R exact) within (1 +- u).
+// With a margin of 2^-20 = 16u, s - R^2 > 2^-20 R^2 proves "no collision" and s - R^2 <
+// -2^-20 R^2 proves "collision" (the subtraction adds at most one more rounding, well inside
+// the margin).  If any pair of a tile falls inside that band, the whole tile is redone with the
+// exact integer test above; tiles with larger coordinates use the integer test throughout.
+// The per-row bookkeeping is kept out of the row loop: each row's ballot is parked in shared
+// memory by lane 0, and the validity mask (columns and rows below n, j < i on the diagonal) is
+// applied once per word.
 #include "td_device.cuh"
 #include "td_internal.h"
 #include "td_tiles.cuh"
@@ -30,15 +42,33 @@ __device__ __forceinline__ uint32_t absdiff(int32_t a, int32_t b)
     return static_cast<uint32_t>(d < 0 ? -d : d);
 }
 
+__device__ __forceinline__ bool exact_hit(const int4 &p, const int4 &q)
+{
+    const uint32_t R = static_cast<uint32_t>(p.w + q.w), R1 = R + 1;
+    const uint32_t dx = min(absdiff(p.x, q.x), R1);
+    const uint32_t dy = min(absdiff(p.y, q.y), R1);
+    const uint32_t dz = min(absdiff(p.z, q.z), R1);
+    return dx * dx + dy * dy + dz * dz <= R * R;
+}
+
+__device__ __forceinline__ bool small_coords(const int4 &p)
+{
+    const int32_t lim = 1 << 23;
+    return p.x > -lim && p.x < lim && p.y > -lim && p.y < lim && p.z > -lim && p.z < lim;
+}
+
 template <class Tiles, bool P>
 __global__ void __launch_bounds__(32 * kWarps)
     k_collide(Tiles tiles, const int32_t *__restrict__ c, const int32_t *__restrict__ rad, uint32_t n,
               uint32_t *__restrict__ table)
 {
     __shared__ int4 rows[kWarps][32];
+    __shared__ float4 rowsf[kWarps][32];
+    __shared__ uint32_t words[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t first = uint64_t(blockIdx.x) * kWarps + warp;
     const uint64_t stride = P ? uint64_t(gridDim.x) * kWarps : tiles.units;
+    constexpr float kTol = 0x1p-20f;
     for (uint64_t u = first; u < tiles.units; u += stride) {
         uint32_t bi, bj;
         if (!tiles(u, bi, bj)) continue;  // warp-uniform
@@ -46,26 +76,44 @@ __global__ void __launch_bounds__(32 * kWarps)
         int4 pj = make_int4(0, 0, 0, 0), pi = make_int4(0, 0, 0, 0);
         if (j < n) pj = make_int4(__ldg(c + 3 * uint64_t(j)), __ldg(c + 3 * uint64_t(j) + 1), __ldg(c + 3 * uint64_t(j) + 2), __ldg(rad + j));
         if (ir < n) pi = make_int4(__ldg(c + 3 * uint64_t(ir)), __ldg(c + 3 * uint64_t(ir) + 1), __ldg(c + 3 * uint64_t(ir) + 2), __ldg(rad + ir));
+        const float4 fj = make_float4(float(pj.x), float(pj.y), float(pj.z), float(pj.w));
         __syncwarp();
         rows[warp][lane] = pi;
+        rowsf[warp][lane] = make_float4(float(pi.x), float(pi.y), float(pi.z), float(pi.w));
         __syncwarp();
-        const bool diag = bi == bj;
-        const uint32_t rows_valid = n - 32 * bi >= 32 ? 32u : n - 32 * bi;  // rows of this tile below n
-        uint32_t word = 0;
-#pragma unroll 4
-        for (int r = 0; r < 32; ++r) {
-            const int4 p = rows[warp][r];
-            const uint32_t R = static_cast<uint32_t>(p.w + pj.w), R1 = R + 1;
-            const uint32_t dx = min(absdiff(p.x, pj.x), R1);
-            const uint32_t dy = min(absdiff(p.y, pj.y), R1);
-            const uint32_t dz = min(absdiff(p.z, pj.z), R1);
-            const uint32_t s = dx * dx + dy * dy + dz * dz;
-            const bool hit = s <= R * R && j < n && uint32_t(r) < rows_valid && (!diag || lane < r);
-            const uint32_t b = __ballot_sync(0xffffffffu, hit);
-            if (lane == r) word = b;
+        bool exact = !__all_sync(0xffffffffu, small_coords(pj) && small_coords(pi));
+        if (!exact) {
+            // FP32 pass: one ballot per row, its word parked in shared memory by lane 0; a pair
+            // within the relative band 2^-20 of R^2 marks the tile for the exact pass
+            bool band = false;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const float4 p = rowsf[warp][r];
+                const float dx = p.x - fj.x, dy = p.y - fj.y, dz = p.z - fj.z;
+                const float s = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const float R = p.w + fj.w, R2 = R * R;
+                const float diff = s - R2;
+                band = band || fabsf(diff) <= R2 * kTol;
+                const uint32_t b = __ballot_sync(0xffffffffu, diff <= 0.0f);
+                if (lane == 0) words[warp][r] = b;
+            }
+            exact = __any_sync(0xffffffffu, band);
         }
+        if (exact) {  // integer pass for the whole tile (large coordinates, or a pair in the band)
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t b = __ballot_sync(0xffffffffu, exact_hit(rows[warp][r], pj));
+                if (lane == 0) words[warp][r] = b;
+            }
+        }
+        __syncwarp();
+        // lane r owns row 32 bi + r: keep columns below n, rows below n, and j < i on the diagonal
+        const uint32_t colmask = __ballot_sync(0xffffffffu, j < n);
+        const uint32_t rows_valid = n - 32 * bi >= 32 ? 32u : n - 32 * bi;
+        const uint32_t valid = uint32_t(lane) < rows_valid ? (colmask & (bi == bj ? ((1u << lane) - 1u) : ~0u)) : 0u;
         const uint64_t t = tri(bi) + bj;
-        table[t * 32 + lane] = word;
+        table[t * 32 + lane] = words[warp][lane] & valid;
+        __syncwarp();
     }
 }
 

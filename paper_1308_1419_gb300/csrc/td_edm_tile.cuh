@@ -2,8 +2,9 @@
 // arXiv:1308.1419), shared by td_edm (rho 64/128) and the batched distance map.
 //
 // One CTA of 256 threads computes one rho x rho block of the packed lower triangle.  The
-// block's rho row points and rho column points are staged in shared memory, KC features at a
-// time, feature-major; each thread keeps a TM x TM register tile (TM = rho / 16) for rows
+// block's rho row points and rho column points are staged in shared memory by asynchronous
+// copies, KC features at a time, feature-major and double-buffered (chunk c + 1 loads while
+// chunk c is consumed); each thread keeps a TM x TM register tile (TM = rho / 16) for rows
 // {tr + 16 a} and columns {tc + 16 b}, so every feature step is two 128-bit shared loads and
 // TM^2 subtract/FMA pairs.  The shared-memory slot of row r is (r mod 16) TM + floor(r / 16):
 // the TM rows a thread owns sit side by side.  With X2, two columns go through each packed
@@ -44,20 +45,53 @@ __device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, un
     return r;
 }
 
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 writes a zero without reading.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 template <int RHO, int KC, bool X2>
 struct EdmTile {
     static constexpr int TM = RHO / 16;
     static constexpr int LD = RHO + 4;  // padded row of a feature plane, keeps 16-byte alignment
-    static constexpr int SMEM_FLOATS = 2 * KC * LD;
+    static constexpr int STAGE_FLOATS = 2 * KC * LD;     // rows and columns of one feature chunk
+    static constexpr int SMEM_FLOATS = 2 * STAGE_FLOATS;  // double-buffered
     static_assert(TM % 4 == 0, "TM must be a multiple of 4");
 
-    __device__ static __forceinline__ int slot(int r) { return (r & 15) * TM + (r >> 4); }
+    // Slot of row (or column) r = t + 16 b (t = r mod 16, b = r / 16) in a feature plane: thread t
+    // reads its TM values as TM/4 16-byte granules t, t + 16, t + 32, ...; granule g holds
+    // b = 4 (g / 16) .. +3.  Consecutive threads read consecutive granules: no bank conflicts.
+    __device__ static __forceinline__ int slot(int r)
+    {
+        const int t = r & 15, b = r >> 4;
+        return (((b >> 2) << 4) + t) * 4 + (b & 3);
+    }
 
+    // Issues the asynchronous copies of features [k0, k0 + kc) of the block's rows and columns.
+    __device__ static __forceinline__ void stage(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0,
+                                                 uint32_t j0, bool diag, uint32_t k0, int kc, float *buf)
+    {
+        float *sA = buf, *sB = buf + KC * LD;
+        for (int e = threadIdx.x; e < RHO * kc; e += 256) {
+            const int r = e % RHO, kk = e / RHO;
+            const uint32_t i = i0 + r, j = j0 + r, k = k0 + kk;
+            cp_async4(sA + kk * LD + slot(r), i < n ? x + uint64_t(i) * d + k : x, i < n ? 4u : 0u);
+            if (!diag) cp_async4(sB + kk * LD + slot(r), j < n ? x + uint64_t(j) * d + k : x, j < n ? 4u : 0u);
+        }
+        cp_async_commit();
+    }
+
+    // sm: SMEM_FLOATS floats.  All 256 threads of the CTA call it together.
     __device__ static void run(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
                                float *__restrict__ out, float *sm)
     {
         const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
-        float *sA = sm, *sB = sm + KC * LD;
         const bool diag = i0 == j0;
         float acc[TM][TM];
         unsigned long long acc2[TM][TM / 2];
@@ -70,26 +104,31 @@ struct EdmTile {
 #pragma unroll
             for (int b = 0; b < TM / 2; ++b) acc2[a][b] = 0ull;
 
-        for (uint32_t k0 = 0; k0 < d; k0 += KC) {
+        const uint32_t nchunks = (d + KC - 1) / KC;
+        stage(x, n, d, i0, j0, diag, 0, d < uint32_t(KC) ? int(d) : KC, sm);
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            const uint32_t k0 = c * KC;
             const int kc = d - k0 < uint32_t(KC) ? int(d - k0) : KC;  // features in this chunk
-            for (int e = tid; e < RHO * kc; e += 256) {
-                const int r = e % RHO, kk = e / RHO;
-                const uint32_t k = k0 + kk;
-                const uint32_t i = i0 + r, j = j0 + r;
-                sA[kk * LD + slot(r)] = i < n ? __ldg(x + uint64_t(i) * d + k) : 0.0f;
-                if (!diag) sB[kk * LD + slot(r)] = j < n ? __ldg(x + uint64_t(j) * d + k) : 0.0f;
+            if (c + 1 < nchunks) {
+                const uint32_t k1 = k0 + KC;
+                stage(x, n, d, i0, j0, diag, k1, d - k1 < uint32_t(KC) ? int(d - k1) : KC,
+                      sm + ((c + 1) & 1) * STAGE_FLOATS);
+                cp_async_wait<1>();  // chunk c has landed; chunk c + 1 may still be in flight
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
-            const float *B = diag ? sA : sB;
+            const float *sA = sm + (c & 1) * STAGE_FLOATS;
+            const float *B = diag ? sA : sA + KC * LD;
 #pragma unroll 2
             for (int kk = 0; kk < kc; ++kk) {
                 float av[TM], bv[TM];
 #pragma unroll
-                for (int q = 0; q < TM; q += 4) {
-                    const float4 va = *reinterpret_cast<const float4 *>(sA + kk * LD + tr * TM + q);
-                    const float4 vb = *reinterpret_cast<const float4 *>(B + kk * LD + tc * TM + q);
-                    av[q] = va.x; av[q + 1] = va.y; av[q + 2] = va.z; av[q + 3] = va.w;
-                    bv[q] = vb.x; bv[q + 1] = vb.y; bv[q + 2] = vb.z; bv[q + 3] = vb.w;
+                for (int h = 0; h < TM / 4; ++h) {
+                    const float4 va = *reinterpret_cast<const float4 *>(sA + kk * LD + (h * 16 + tr) * 4);
+                    const float4 vb = *reinterpret_cast<const float4 *>(B + kk * LD + (h * 16 + tc) * 4);
+                    av[4 * h] = va.x; av[4 * h + 1] = va.y; av[4 * h + 2] = va.z; av[4 * h + 3] = va.w;
+                    bv[4 * h] = vb.x; bv[4 * h + 1] = vb.y; bv[4 * h + 2] = vb.z; bv[4 * h + 3] = vb.w;
                 }
                 if (X2) {
                     unsigned long long b2[TM / 2];
@@ -114,7 +153,7 @@ struct EdmTile {
                         }
                 }
             }
-            __syncthreads();
+            __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
         }
         if (X2) {
 #pragma unroll

@@ -72,6 +72,8 @@ _c_gram = _sig("td_edm_gram", _int, _vp, _u32, _u32, _vp, _vp, C.c_size_t, _vp)
 _c_gram_status = _sig("td_edm_gram_status", _int, _vp, C.POINTER(C.c_uint64), _vp)
 _c_batched_noalloc = _sig("td_edm_batched_noalloc", _int, _u32, _vp, _vp, _vp, _vp,
                           C.POINTER(td_batched_config), _stats_p, _vp)
+_c_partition = _sig("td_partition", _int, _u32, _u32, _u32, _u32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                    C.POINTER(C.c_uint64), C.POINTER(C.c_uint64))
 _c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
 _c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
 _c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
@@ -96,9 +98,11 @@ def _stream(stream):
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
-def _dev(t, dtype, numel, name):
-    if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError(f"{name} must be a CUDA tensor")
+def _dev(t, dtype, numel, name, host_ok=False):
+    """Device address of t.  host_ok: a pinned host tensor is accepted too -- its address is
+    valid on the device (unified addressing), so a kernel writes it in place over the host link."""
+    if not isinstance(t, torch.Tensor) or not (t.is_cuda or (host_ok and t.is_pinned())):
+        raise TypeError(f"{name} must be a CUDA tensor" + (" or a pinned host tensor" if host_ok else ""))
     if t.dtype != dtype:
         raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
     if not t.is_contiguous():
@@ -139,14 +143,22 @@ def td_plan(mapping, schedule, N: int, rho: int) -> dict:
     return st.as_dict()
 
 
+def td_partition(N: int, rho: int, G: int, r: int):
+    """Rank r's block rows [br0, br1) and packed-output slice [off0, off1) (host only)."""
+    b0, b1, o0, o1 = C.c_uint32(), C.c_uint32(), C.c_uint64(), C.c_uint64()
+    _check(_c_partition(N, rho, G, r, C.byref(b0), C.byref(b1), C.byref(o0), C.byref(o1)))
+    return int(b0.value), int(b1.value), int(o0.value), int(o1.value)
+
+
 # ---------------------------------------------------------------- mapping kernels
 
 def td_map_probe(mapping, schedule, N: int, rho: int, out: torch.Tensor = None, stream=None):
-    """Probe output (int32 tensor holding the uint32 bit patterns) and launch stats."""
+    """Probe output (int32 tensor holding the uint32 bit patterns) and launch stats.  out may be
+    a device tensor or a pinned host tensor (written in place by the kernel)."""
     total = td_tri_size(N)
     if out is None:
         out = torch.empty(max(total, 1), dtype=torch.int32, device="cuda")
-    ptr = _dev(out, torch.int32, total, "out")
+    ptr = _dev(out, torch.int32, total, "out", host_ok=True)
     st = td_launch_stats()
     _check(_c_map_probe(_mapping(mapping), _schedule(schedule), N, rho, ptr, C.byref(st), _stream(stream)))
     return out, st.as_dict()

@@ -79,14 +79,14 @@ def test_edm_ragged_all_kernels(d):
 def test_edm_f32x2_matches_scalar():
     xh = synth.uniform_points(700, 64, 77)
     x = torch.from_numpy(xh).cuda()
-    assert td.td_get_option("edm_f32x2") == 1
+    assert td.td_get_option("edm_f32x2") == 0
     a, _ = _edm("LTM", "persistent", x, 128)
-    td.td_set_option("edm_f32x2", 0)
+    td.td_set_option("edm_f32x2", 1)
     try:
         b, _ = _edm("LTM", "persistent", x, 128)
         c, _ = _edm("LTM", "persistent", x, 64)
     finally:
-        td.td_set_option("edm_f32x2", 1)
+        td.td_set_option("edm_f32x2", 0)
     assert np.array_equal(a.view(np.uint32), b.view(np.uint32))
     assert np.array_equal(a.view(np.uint32), c.view(np.uint32))
 
