@@ -6,22 +6,26 @@
 // every pair with D^2 < 1e-2 (|x_i|^2 + |x_j|^2) -- the diagonal included -- is recomputed in the
 // direct FP32 form sum_k (x_i[k] - x_j[k])^2 from the FP32 points.
 //
-// Layout of the work: 128 x 128 blocks of the packed lower triangle, issued by g(lambda) over the
-// tile triangle of side ceil(n / 128) (Sec. II-A), one persistent CTA per SM.  Per block:
-//   1. thread 0 issues TMA loads of the block's 128 row points and 128 column points (BF16,
-//      64-feature boxes of 128 rows x 128 bytes, 128-byte swizzle) -- one set for a diagonal block;
-//   2. one thread issues d/16 tcgen05.mma (M = N = 128, K = 16) into a 128-column FP32 TMEM
-//      accumulator and commits to an mbarrier;
-//   3. sixteen epilogue warps read the accumulator (warp w: TMEM lanes 32 (w mod 4) .., columns
-//      32 (w / 4) ..), form D^2, queue the cancelling pairs in shared memory, take the square
-//      root of the rest, and write rows through a per-warp shared-memory transpose so that each
-//      store instruction covers 32 consecutive floats of one packed row;
-//   4. the block's FP32 row and column points are staged by TMA into the (now free) operand
-//      region, 128 features at a time, and the warps recompute the queued pairs from shared
-//      memory -- up to 32 pairs per warp per round, lanes striding the features, partial sums
-//      combined in a fixed butterfly order.
-// Every mbarrier wait is bounded; a timeout records an error code in the workspace status word,
-// releases the tensor memory and ends the CTA.
+// Three kernels, stream-ordered:
+//   k_gram_prep  BF16 copy of the points and FP32 squared norms.
+//   k_gram       persistent, warp-specialised, one CTA per SM; 128 x 128 blocks of the packed lower
+//                triangle issued by g(lambda) over the block triangle of side ceil(n / 128)
+//                (Sec. II-A), every role walking the same block sequence:
+//                  warp 0    TMA producer: 64-feature boxes (128 rows x 128 bytes, 128-byte swizzle)
+//                            of the block's row and column points into a 4-stage ring;
+//                  warp 1    MMA issuer: tcgen05.mma (M = N = 128, K = 16) into one of two FP32 TMEM
+//                            accumulators, each ring stage released by tcgen05.commit;
+//                  warps 2-9 epilogue: read the accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
+//                            columns 64 ((w - 2) / 4) ..), form D^2, append the cancelling pairs to a
+//                            global queue (one atomic per warp and 32 columns), take the square root
+//                            of the rest and write packed rows through a per-warp transpose, then
+//                            release the accumulator.
+//                The two accumulators let the next block's loads and MMAs run under the epilogue.
+//   k_gram_fix   recomputes the queued pairs in the direct form: one warp per 4 pairs, 16-byte loads,
+//                lanes striding the features, partial sums combined in a fixed butterfly order.
+// If the queue is full, the epilogue recomputes the extra pairs itself.  Every mbarrier wait is
+// bounded; a timeout records an error code in the workspace status word and the roles wind down,
+// the tensor memory is released and the CTA ends.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -32,40 +36,25 @@
 namespace td {
 namespace {
 
-constexpr uint32_t BM = 128;          // block side (rows and columns)
-constexpr uint32_t BK = 64;           // features per BF16 TMA box (128 bytes)
-constexpr uint32_t MAXKB = 4;         // BF16 boxes per operand: d <= 256
-constexpr uint32_t BOX = BM * BK * 2; // 16 KB
-constexpr uint32_t KF = 128;          // features per FP32 staging phase of the recompute (512 bytes)
-constexpr uint32_t THREADS = 512;     // 16 warps
-constexpr uint32_t WARPS = THREADS / 32;
-constexpr uint32_t SLD = 33;          // padded row of the transpose stage
-constexpr uint32_t PAIRS_PER_WARP = 32;  // recomputed pairs a warp holds per round
+constexpr uint32_t BM = 128;           // block side (rows and columns)
+constexpr uint32_t BK = 64;            // features per BF16 TMA box (128 bytes)
+constexpr uint32_t BOX = BM * BK * 2;  // 16 KB
+constexpr uint32_t STAGES = 4;         // ring stages, one box of rows and one of columns each
+constexpr uint32_t EPI_WARPS = 8;
+constexpr uint32_t THREADS = 32 * (2 + EPI_WARPS);
+constexpr uint32_t SLD = 33;           // padded row of the transpose stage
+constexpr uint32_t TMEM_COLS = 256;    // two 128-column FP32 accumulators
+constexpr float kCancel = 1e-2f;       // recompute when D^2 < kCancel (|x_i|^2 + |x_j|^2)
 
-// Shared-memory layout (offsets from a 1024-byte aligned base).  The 128 KB operand region is
-// used three ways in turn within a block: BF16 operands (TMA -> MMA), then the epilogue's
-// transpose stage, then FP32 point features for the recompute (rows at 0, columns at 64 KB).
-constexpr uint32_t OFF_A = 0;
-constexpr uint32_t OFF_B = OFF_A + MAXKB * BOX;
-constexpr uint32_t OFF_STAGE = 0;
-constexpr uint32_t OFF_FROW = 0;
-constexpr uint32_t OFF_FCOL = BM * KF * 4;
-constexpr uint32_t OFF_QUEUE = OFF_B + MAXKB * BOX;
-constexpr uint32_t OFF_NROW = OFF_QUEUE + BM * BM * 2;
-constexpr uint32_t OFF_NCOL = OFF_NROW + BM * 4;
-constexpr uint32_t OFF_CTRL = OFF_NCOL + BM * 4;
-constexpr uint32_t SMEM_USED = OFF_CTRL + 64;
+constexpr uint32_t OFF_RING = 0;
+constexpr uint32_t OFF_STAGE = OFF_RING + STAGES * 2 * BOX;
+constexpr uint32_t OFF_BAR = OFF_STAGE + EPI_WARPS * 32 * SLD * 4;
+constexpr uint32_t SMEM_USED = OFF_BAR + 128;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;  // slack for aligning the base
-static_assert(OFF_B % 1024 == 0, "operand tiles must be 1024-byte aligned");
-static_assert(WARPS * 32 * SLD * 4 <= 2 * MAXKB * BOX, "transpose stage must fit the operand region");
-static_assert(2 * BM * KF * 4 <= 2 * MAXKB * BOX, "recompute staging must fit the operand region");
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
-constexpr uint32_t TMEM_COLS = 128;
-constexpr float kCancel = 1e-2f;  // recompute when D^2 < kCancel (|x_i|^2 + |x_j|^2)
-
-// workspace status words (uint32): [0] error code, [1] reserved, [2..3] recomputed pairs (uint64)
-enum : uint32_t { kErrNone = 0, kErrTmaWait = 1, kErrMmaWait = 2, kErrStageWait = 3 };
+// workspace status words (uint32): [0] error code, [1] reserved, [2..3] queued pairs (uint64)
+enum : uint32_t { kErrNone = 0, kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3 };
 
 __device__ __forceinline__ float sqrt_approx(float v)
 {
@@ -92,9 +81,21 @@ __global__ void __launch_bounds__(256) k_gram_prep(const float *__restrict__ x, 
     if (lane == 0) norms[warp] = s;
 }
 
+// Direct FP32 distance of one pair, sequential over the features (the epilogue's overflow path).
+__device__ float direct_distance(const float *__restrict__ x, uint32_t d, uint32_t i, uint32_t j)
+{
+    const float *xi = x + uint64_t(i) * d, *xj = x + uint64_t(j) * d;
+    float s = 0.0f;
+    for (uint32_t k = 0; k < d; ++k) {
+        const float t = __ldg(xi + k) - __ldg(xj + k);
+        s = fmaf(t, t, s);
+    }
+    return sqrtf(s);
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gram(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap fmap,
-           const float *__restrict__ norms, uint32_t n, uint32_t d, uint32_t nt, float *__restrict__ out,
+    k_gram(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ x, const float *__restrict__ norms,
+           uint32_t n, uint32_t d, uint32_t nt, float *__restrict__ out, uint2 *__restrict__ queue, uint64_t qcap,
            uint32_t *__restrict__ status)
 {
     using namespace sm100;
@@ -102,32 +103,32 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t base = smem_u32(sm);
-    float *stage_all = reinterpret_cast<float *>(sm + OFF_STAGE);
-    const float *frow = reinterpret_cast<const float *>(sm + OFF_FROW);
-    uint16_t *queue = reinterpret_cast<uint16_t *>(sm + OFF_QUEUE);
-    float *nrow = reinterpret_cast<float *>(sm + OFF_NROW);
-    float *ncol = reinterpret_cast<float *>(sm + OFF_NCOL);
-    uint32_t *ctrl = reinterpret_cast<uint32_t *>(sm + OFF_CTRL);
-    const uint32_t tma_bar = base + OFF_CTRL, mma_bar = base + OFF_CTRL + 8, stage_bar = base + OFF_CTRL + 16;
-    uint32_t *tmem_slot = ctrl + 6;
-    uint32_t *qcount = ctrl + 8;  // two counters, alternating by block
-    uint32_t *abort_flag = ctrl + 10;
+    const uint32_t bar = base + OFF_BAR;  // full[4], empty[4], tfull[2], tempty[2], then tmem slot, abort
+    auto full_bar = [&](uint32_t s) { return bar + 8 * s; };
+    auto empty_bar = [&](uint32_t s) { return bar + 8 * (STAGES + s); };
+    auto tfull_bar = [&](uint32_t a) { return bar + 8 * (2 * STAGES + a); };
+    auto tempty_bar = [&](uint32_t a) { return bar + 8 * (2 * STAGES + 2 + a); };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 8 * (2 * STAGES + 4));
+    volatile uint32_t *abort_flag = tmem_slot + 1;
+    unsigned long long *qcount = reinterpret_cast<unsigned long long *>(status + 2);
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t nkb = (d + BK - 1) / BK;
-    const uint32_t nph = (d + KF - 1) / KF;
-    const uint32_t idesc = umma_idesc_bf16_f32(BM, BM);
+    const uint64_t tiles = tri(nt);
 
     if (tid == 0) {
-        mbar_init(tma_bar, 1);
-        mbar_init(mma_bar, 1);
-        mbar_init(stage_bar, 1);
+        for (uint32_t s2 = 0; s2 < STAGES; ++s2) {
+            mbar_init(full_bar(s2), 1);
+            mbar_init(empty_bar(s2), 1);
+        }
+        for (uint32_t a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), EPI_WARPS);
+        }
         fence_mbar_init();
-        qcount[0] = 0;
-        qcount[1] = 0;
         *abort_flag = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
         tmem_relinquish();
     }
@@ -136,160 +137,187 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    uint32_t phase = 0, sphase = 0, it = 0;
-    uint64_t recomputed = 0;
-    const uint64_t tiles = tri(nt);
-    for (uint64_t lam = blockIdx.x; lam < tiles; lam += gridDim.x, ++it) {
-        uint32_t bi, bj;
-        ltm_g(lam, bi, bj);
-        const bool diag = bi == bj;
-        uint32_t *qc = qcount + (it & 1);
-        if (tid < BM) {
-            const uint32_t r = bi * BM + tid;
-            nrow[tid] = r < n ? norms[r] : 0.0f;
-        } else if (tid < 2 * BM) {
-            const uint32_t c = bj * BM + (tid - BM);
-            ncol[tid - BM] = c < n ? norms[c] : 0.0f;
-        }
-        if (tid == 0) {
-            qcount[(it + 1) & 1] = 0;  // counter of the next block; its last readers passed the previous barrier
-            mbar_arrive_expect_tx(tma_bar, nkb * BOX * (diag ? 1u : 2u));
-            for (uint32_t kb = 0; kb < nkb; ++kb) {
-                tma_load_2d(base + OFF_A + kb * BOX, &tmap, int32_t(kb * BK), int32_t(bi * BM), tma_bar);
-                if (!diag) tma_load_2d(base + OFF_B + kb * BOX, &tmap, int32_t(kb * BK), int32_t(bj * BM), tma_bar);
+    auto fail_role = [&](uint32_t code) {
+        atomicCAS(status, kErrNone, code);  // keep the first error
+        *abort_flag = 1;
+    };
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            uint64_t g = 0;  // boxes issued so far: stage g % STAGES, round g / STAGES
+            for (uint64_t lam = blockIdx.x; lam < tiles && !*abort_flag; lam += gridDim.x) {
+                uint32_t bi, bj;
+                ltm_g(lam, bi, bj);
+                const bool diag = bi == bj;
+                for (uint32_t kb = 0; kb < nkb; ++kb, ++g) {
+                    const uint32_t s2 = uint32_t(g % STAGES), round = uint32_t(g / STAGES);
+                    if (!mbar_wait(empty_bar(s2), (round & 1u) ^ 1u)) {
+                        fail_role(kErrProducer);
+                        break;
+                    }
+                    const uint32_t dstA = base + OFF_RING + s2 * 2 * BOX, dstB = dstA + BOX;
+                    mbar_arrive_expect_tx(full_bar(s2), diag ? BOX : 2 * BOX);
+                    tma_load_2d(dstA, &tmap, int32_t(kb * BK), int32_t(bi * BM), full_bar(s2));
+                    if (!diag) tma_load_2d(dstB, &tmap, int32_t(kb * BK), int32_t(bj * BM), full_bar(s2));
+                }
             }
         }
-        __syncthreads();
-        if (warp == 0) {
-            const bool ok = mbar_wait(tma_bar, phase);
-            if (!ok && lane == 0) {
-                atomicCAS(status, kErrNone, kErrTmaWait);  // keep the first error
-                *abort_flag = 1;
-            }
-            if (ok && lane == 0) {
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_bf16_f32(BM, BM);
+            uint64_t g = 0, t = 0;
+            for (uint64_t lam = blockIdx.x; lam < tiles && !*abort_flag; lam += gridDim.x, ++t) {
+                uint32_t bi, bj;
+                ltm_g(lam, bi, bj);
+                const bool diag = bi == bj;
+                const uint32_t a = uint32_t(t & 1), use = uint32_t(t >> 1);
+                if (!mbar_wait(tempty_bar(a), (use & 1u) ^ 1u)) {
+                    fail_role(kErrMma);
+                    break;
+                }
                 tc_fence_after();
-                const uint32_t bsrc = diag ? OFF_A : OFF_B;
-                for (uint32_t kb = 0; kb < nkb; ++kb)
+                const uint32_t dacc = tmem + a * BM;
+                bool ok = true;
+                for (uint32_t kb = 0; kb < nkb; ++kb, ++g) {
+                    const uint32_t s2 = uint32_t(g % STAGES), round = uint32_t(g / STAGES);
+                    if (!mbar_wait(full_bar(s2), round & 1u)) {
+                        fail_role(kErrMma);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t srcA = base + OFF_RING + s2 * 2 * BOX, srcB = diag ? srcA : srcA + BOX;
 #pragma unroll
                     for (uint32_t k = 0; k < BK / 16; ++k) {
                         if (kb * BK + k * 16 >= d) break;
-                        const uint64_t a = umma_desc_sw128(base + OFF_A + kb * BOX + k * 32);
-                        const uint64_t b = umma_desc_sw128(base + bsrc + kb * BOX + k * 32);
-                        umma_bf16(tmem, a, b, idesc, (kb | k) != 0);
+                        umma_bf16(dacc, umma_desc_sw128(srcA + k * 32), umma_desc_sw128(srcB + k * 32), idesc,
+                                  (kb | k) != 0);
                     }
-                umma_commit(mma_bar);
+                    umma_commit(empty_bar(s2));  // the stage is free once these MMAs complete
+                }
+                if (!ok) break;
+                umma_commit(tfull_bar(a));  // the accumulator is ready once all MMAs complete
             }
-            __syncwarp();
         }
-        // warp-uniform, since the tensor-memory loads below are .sync.aligned
-        const bool mma_ok = __all_sync(0xffffffffu, mbar_wait(mma_bar, phase));
-        if (!mma_ok && lane == 0) {
-            atomicCAS(status, kErrNone, kErrMmaWait);
-            *abort_flag = 1;
-        }
-        phase ^= 1;
-        tc_fence_after();
-        if (mma_ok) {
-            // ---- epilogue: warp w reads TMEM lanes 32 (w mod 4) .. +32, columns 32 (w / 4) .. +32;
-            // the operand region is free now and holds the per-warp transpose stages
-            const uint32_t q = warp & 3, c0 = 32 * (warp >> 2);
+    } else {
+        // ---------------- epilogue warps
+        const uint32_t ew = warp - 2, q = warp & 3, half = ew >> 2;
+        float *st = reinterpret_cast<float *>(sm + OFF_STAGE) + ew * 32 * SLD;
+        uint64_t t = 0;
+        for (uint64_t lam = blockIdx.x; lam < tiles; lam += gridDim.x, ++t) {
+            if (*abort_flag) break;
+            uint32_t bi, bj;
+            ltm_g(lam, bi, bj);
+            const uint32_t a = uint32_t(t & 1), use = uint32_t(t >> 1);
+            const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull_bar(a), use & 1u));
+            if (!ready) {
+                if (lane == 0) fail_role(kErrEpilogue);
+                break;
+            }
+            tc_fence_after();
             const uint32_t rl = 32 * q + lane, i = bi * BM + rl;
-            const float ni = nrow[rl];
-            float *st = stage_all + warp * 32 * SLD;
-            float v[32];
-            tmem_ld_32x32b_x32(tmem + ((32 * q) << 16) + c0, v);
+            const float ni = i < n ? __ldg(norms + i) : 0.0f;
+#pragma unroll 1
+            for (uint32_t c = 0; c < 2; ++c) {
+                const uint32_t c0 = 64 * half + 32 * c;
+                const uint32_t jl = bj * BM + c0 + lane;
+                const float njl = jl < n ? __ldg(norms + jl) : 0.0f;  // lane l holds column c0 + l's norm
+                float v[32];
+                tmem_ld_32x32b_x32(tmem + a * BM + ((32 * q) << 16) + c0, v);
+                uint32_t mask = 0;
 #pragma unroll
-            for (uint32_t cc = 0; cc < 32; ++cc) {
-                const uint32_t jl = c0 + cc, j = bj * BM + jl;
-                const float s = ni + ncol[jl];
-                const float d2 = fmaf(-2.0f, v[cc], s);
-                const bool cancel = d2 < kCancel * s;
-                if (cancel && i < n && j <= i) {
-                    const uint32_t slot = atomicAdd(qc, 1u);
-                    queue[slot] = static_cast<uint16_t>((rl << 7) | jl);
+                for (uint32_t cc = 0; cc < 32; ++cc) {
+                    const uint32_t j = bj * BM + c0 + cc;
+                    const float s2 = ni + __shfl_sync(0xffffffffu, njl, cc);
+                    const float d2 = fmaf(-2.0f, v[cc], s2);
+                    const bool cancel = d2 < kCancel * s2;
+                    if (cancel && i < n && j <= i) mask |= 1u << cc;
+                    st[lane * SLD + cc] = cancel ? 0.0f : sqrt_approx(d2);
                 }
-                st[lane * SLD + cc] = cancel ? 0.0f : sqrt_approx(d2);
-            }
-            __syncwarp();
-            const uint32_t j2 = bj * BM + c0 + lane;
+                // append this warp's cancelling pairs with one atomic: an exclusive scan of the
+                // per-lane counts gives each lane its slots
+                const uint32_t cnt = __popc(mask);
+                uint32_t pre = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (lane >= uint32_t(o)) pre += y;
+                }
+                const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
+                pre -= cnt;
+                unsigned long long slot0 = 0;
+                if (total) {
+                    if (lane == 31) slot0 = atomicAdd(qcount, (unsigned long long)total);
+                    slot0 = __shfl_sync(0xffffffffu, slot0, 31);
+                }
+                uint64_t slot = slot0 + pre;
+                for (uint32_t m = mask; m; m &= m - 1, ++slot) {
+                    const uint32_t cc = __ffs(m) - 1, j = bj * BM + c0 + cc;
+                    if (slot < qcap) queue[slot] = make_uint2(i, j);
+                    else st[lane * SLD + cc] = direct_distance(x, d, i, j);  // queue full: recompute here
+                }
+                __syncwarp();
+                const uint32_t j2 = bj * BM + c0 + lane;
 #pragma unroll 4
-            for (uint32_t rr = 0; rr < 32; ++rr) {
-                const uint32_t i2 = bi * BM + 32 * q + rr;
-                if (i2 < n && j2 <= i2) out[tri(i2) + j2] = st[rr * SLD + lane];
+                for (uint32_t rr = 0; rr < 32; ++rr) {
+                    const uint32_t i2 = bi * BM + 32 * q + rr;
+                    if (i2 < n && j2 <= i2) out[tri(i2) + j2] = st[rr * SLD + lane];
+                }
+                __syncwarp();
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(a));
         }
-        fence_proxy_async_smem();  // the stage's generic accesses precede the staging TMA below
-        tc_fence_before();
-        __syncthreads();
-        if (*abort_flag) break;
-        // ---- direct FP32 recompute of the cancelling pairs.  The block's row and column points
-        // are staged by TMA, KF features per phase, into the operand region; each warp holds up
-        // to 32 pairs per round, its lanes striding the features, and the per-lane partial sums
-        // are combined in a fixed butterfly order at the end.
-        const uint32_t Q = *qc;
-        bool stage_ok = true;
-        for (uint32_t r0 = 0; r0 < Q && stage_ok; r0 += WARPS * PAIRS_PER_WARP) {
-            const uint32_t e0 = r0 + warp * PAIRS_PER_WARP;
-            const uint32_t cnt = e0 < Q ? min(PAIRS_PER_WARP, Q - e0) : 0u;
-            float part[PAIRS_PER_WARP];
-#pragma unroll
-            for (uint32_t t = 0; t < PAIRS_PER_WARP; ++t) part[t] = 0.0f;
-            for (uint32_t ph = 0; ph < nph; ++ph) {
-                if (tid == 0) {
-                    mbar_arrive_expect_tx(stage_bar, BM * KF * 4 * (diag ? 1u : 2u));
-                    tma_load_2d(base + OFF_FROW, &fmap, int32_t(ph * KF), int32_t(bi * BM), stage_bar);
-                    if (!diag) tma_load_2d(base + OFF_FCOL, &fmap, int32_t(ph * KF), int32_t(bj * BM), stage_bar);
-                }
-                const bool got = mbar_wait(stage_bar, sphase);
-                sphase ^= 1;
-                stage_ok = __syncthreads_and(got) != 0;  // CTA-uniform: every thread leaves together
-                if (!stage_ok) {
-                    if (tid == 0) atomicCAS(status, kErrNone, kErrStageWait);
-                    break;
-                }
-                const float *fcol = reinterpret_cast<const float *>(sm + (diag ? OFF_FROW : OFF_FCOL));
-#pragma unroll
-                for (uint32_t t = 0; t < PAIRS_PER_WARP; ++t) {
-                    if (t < cnt) {
-                        const uint32_t code = queue[e0 + t];
-                        const float *xi = frow + (code >> 7) * KF, *xj = fcol + (code & 127u) * KF;
-                        float acc = part[t];
-#pragma unroll
-                        for (uint32_t k = lane; k < KF; k += 32) {
-                            const float tdiff = xi[k] - xj[k];
-                            acc = fmaf(tdiff, tdiff, acc);
-                        }
-                        part[t] = acc;
-                    }
-                }
-                fence_proxy_async_smem();
-                __syncthreads();  // every warp is done with this phase before a TMA overwrites it
-            }
-            if (!stage_ok) break;
-#pragma unroll
-            for (uint32_t t = 0; t < PAIRS_PER_WARP; ++t) {
-                if (t < cnt) {
-                    float s = part[t];
-                    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                    if (lane == 0) {
-                        const uint32_t code = queue[e0 + t];
-                        const uint32_t i = bi * BM + (code >> 7), j = bj * BM + (code & 127u);
-                        out[tri(i) + j] = sqrtf(s);
-                    }
-                }
-            }
-        }
-        recomputed += Q;
-        if (!stage_ok) {
-            if (tid == 0) *abort_flag = 1;
-        }
-        __syncthreads();
-        if (*abort_flag) break;
     }
-    if (tid == 0 && recomputed) atomicAdd(reinterpret_cast<unsigned long long *>(status + 2), recomputed);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// Direct FP32 recompute of the queued pairs: a warp takes 4 pairs at a time, lanes stride the
+// features 4 at a time (16-byte loads), and the per-lane partial sums are combined in a fixed
+// butterfly order.  d is a multiple of 4.
+__global__ void __launch_bounds__(256) k_gram_fix(const float *__restrict__ x, uint32_t d,
+                                                  const uint2 *__restrict__ queue, const uint32_t *__restrict__ status,
+                                                  uint64_t qcap, float *__restrict__ out)
+{
+    const unsigned long long cnt = *reinterpret_cast<const unsigned long long *>(status + 2);
+    const uint64_t total = cnt < qcap ? cnt : qcap;
+    const uint32_t lane = threadIdx.x & 31, d4 = d / 4;
+    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+    for (uint64_t e = (uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; e < total; e += warps * 4) {
+        uint2 pr[4];
+        float part[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            pr[p] = e + p < total ? queue[e + p] : make_uint2(0u, 0u);
+            part[p] = 0.0f;
+        }
+        for (uint32_t k4 = lane; k4 < d4; k4 += 32) {
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + uint64_t(pr[p].x) * d) + k4);
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(x + uint64_t(pr[p].y) * d) + k4);
+                float t = a.x - b.x;
+                part[p] = fmaf(t, t, part[p]);
+                t = a.y - b.y;
+                part[p] = fmaf(t, t, part[p]);
+                t = a.z - b.z;
+                part[p] = fmaf(t, t, part[p]);
+                t = a.w - b.w;
+                part[p] = fmaf(t, t, part[p]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            float s2 = part[p];
+            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            if (lane == 0 && e + p < total) out[tri(pr[p].x) + pr[p].y] = sqrtf(s2);
+        }
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -313,15 +341,19 @@ EncodeTiledFn encode_fn()
 }
 
 struct GramLayout {
-    size_t norms, xb, total;
+    size_t norms, xb, queue, total;
+    uint64_t qcap;
 };
 
+// status (256 B) | norms (n floats) | BF16 points | queue of cancelling pairs (qcap x 8 B)
 GramLayout gram_layout(uint32_t n, uint32_t d)
 {
     GramLayout L;
     L.norms = 256;
     L.xb = (L.norms + size_t(n) * 4 + 1023) & ~size_t(1023);
-    L.total = L.xb + size_t(n) * d * 2;
+    L.queue = (L.xb + size_t(n) * d * 2 + 1023) & ~size_t(1023);
+    L.qcap = tri(n) / 32 + 65536;  // twice the 1/64 fraction of clustered data, plus slack
+    L.total = L.queue + L.qcap * 8;
     return L;
 }
 
@@ -336,6 +368,7 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     auto *status = reinterpret_cast<uint32_t *>(base);
     auto *norms = reinterpret_cast<float *>(base + L.norms);
     auto *xb = reinterpret_cast<__nv_bfloat16 *>(base + L.xb);
+    auto *queue = reinterpret_cast<uint2 *>(base + L.queue);
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     td_status s = cuda_status(cudaMemsetAsync(status, 0, 16, st), "td_edm_gram status reset");
@@ -352,22 +385,18 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
-    // FP32 points for the direct recompute: KF-feature boxes of 128 rows, no swizzle
-    CUtensorMap fmap;
-    const cuuint64_t fstride[1] = {cuuint64_t(d) * 4};
-    const cuuint32_t fbox[2] = {KF, BM};
-    const CUresult r2 = enc(&fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(x), gdim, fstride, fbox,
-                            estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r2 != CUDA_SUCCESS) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled (FP32 points) failed (%d)", int(r2));
     s = cuda_status(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
                     "td_edm_gram shared memory attribute");
     if (s != TD_OK) return s;
     const uint32_t nt = (n + BM - 1) / BM;
     const uint64_t tiles = tri(nt);
     const uint64_t grid = tiles < uint64_t(sm_count()) ? tiles : uint64_t(sm_count());
-    k_gram<<<dim3(static_cast<uint32_t>(grid)), THREADS, SMEM_BYTES, st>>>(tmap, fmap, norms, n, d, nt, out, status);
-    return launch_status("td_edm_gram kernel");
+    k_gram<<<dim3(static_cast<uint32_t>(grid)), THREADS, SMEM_BYTES, st>>>(tmap, x, norms, n, d, nt, out, queue, L.qcap,
+                                                                          status);
+    s = launch_status("td_edm_gram kernel");
+    if (s != TD_OK) return s;
+    k_gram_fix<<<dim3(8 * static_cast<uint32_t>(sm_count())), 256, 0, st>>>(x, d, queue, status, L.qcap, out);
+    return launch_status("td_edm_gram recompute kernel");
 }
 
 td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cudaStream_t st)

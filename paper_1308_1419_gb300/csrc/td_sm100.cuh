@@ -1,7 +1,7 @@
 // td_sm100.cuh -- thin inline-PTX wrappers for the Blackwell (sm_100 family) features libtd
 // uses: mbarriers, TMA tensor loads, and the tcgen05 tensor-core / tensor-memory instructions.
-// Every wait is bounded: after kSpinLimit polls it gives up and reports failure, so a kernel can
-// record an error and leave instead of hanging.
+// Every wait is bounded: after kWaitNs nanoseconds (or kSpinLimit polls) it gives up and reports
+// failure, so a kernel can record an error and leave instead of hanging.
 #pragma once
 
 #include <cstdint>
@@ -10,7 +10,15 @@
 namespace td {
 namespace sm100 {
 
-constexpr uint32_t kSpinLimit = 1u << 26;  // polls of try_wait before a wait is declared failed
+constexpr uint32_t kSpinLimit = 1u << 26;            // polls of try_wait, a backstop
+constexpr uint64_t kWaitNs = 2000000000ull;            // 2 s: far beyond any legitimate wait here
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -54,8 +62,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 // Waits for the phase with the given parity to complete; false if it did not within the limit.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
 {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+    }
     return false;
 }
 

@@ -85,3 +85,15 @@ def test_gram_rejects():
     x = torch.zeros(10, 264, device="cuda")
     with pytest.raises(td.TDError):
         td.td_edm_gram(x)                                  # d > 256
+
+
+def test_gram_queue_overflow_identical_points():
+    """Every pair of identical points cancels: far more pairs than the recompute queue holds, so
+    the epilogue recomputes the overflow itself.  All distances must be exactly 0."""
+    n, d = 2048, 64
+    row = synth.uniform_points(1, d, 5)
+    x = torch.from_numpy(np.repeat(row, n, axis=0)).cuda()
+    out, ws = td.td_edm_gram(x)
+    fb = td.td_edm_gram_status(ws)
+    assert fb == n * (n + 1) // 2
+    assert bool((out[: n * (n + 1) // 2] == 0).all())
