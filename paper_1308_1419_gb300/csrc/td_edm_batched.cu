@@ -46,15 +46,14 @@ size_t batched_workspace_bytes(uint32_t nprob)
 
 namespace {
 
-constexpr int KC = 16;
 constexpr int kSmemPrefix = 1024;  // prefix entries staged in shared memory (larger batches search global)
 
 template <int RHO, bool X2>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(edm_tile_threads(RHO), edm_tile_min_ctas(RHO))
     k_edm_batched(const uint64_t *__restrict__ prefix, const BatchMeta *__restrict__ meta, uint32_t nprob,
                   uint64_t total, const float *__restrict__ x, float *__restrict__ out)
 {
-    using Tile = EdmTile<RHO, KC, X2>;
+    using Tile = typename EdmTileFor<RHO, X2>::type;
     __shared__ __align__(16) float sm[Tile::SMEM_FLOATS];
     __shared__ uint64_t sp[kSmemPrefix + 1];
     const bool staged = nprob <= kSmemPrefix;
@@ -81,14 +80,15 @@ template <int RHO, bool X2>
 td_status launch_rho(const uint64_t *prefix, const BatchMeta *meta, uint32_t nprob, uint64_t total, const float *x,
                      float *out, uint32_t ctas_per_sm, cudaStream_t st, uint64_t *ctas)
 {
+    constexpr int NT = EdmTileFor<RHO, X2>::type::NT;
     auto k = k_edm_batched<RHO, X2>;
-    uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, total);
+    uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), NT, 0, total);
     if (ctas_per_sm > 0) {
         const uint64_t want = uint64_t(ctas_per_sm) * sm_count();
         g = std::min<uint64_t>(std::min(g, want), total);
         if (g == 0) g = 1;
     }
-    k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(prefix, meta, nprob, total, x, out);
+    k<<<dim3(static_cast<uint32_t>(g)), NT, 0, st>>>(prefix, meta, nprob, total, x, out);
     if (ctas) *ctas = g;
     return launch_status("td_edm_batched kernel");
 }

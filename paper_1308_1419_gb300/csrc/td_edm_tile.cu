@@ -8,13 +8,11 @@
 namespace td {
 namespace {
 
-constexpr int KC = 16;
-
 template <class Tiles, int RHO, bool X2, bool P>
-__global__ void __launch_bounds__(256) k_edm_tiled(Tiles tiles, const float *__restrict__ x, uint32_t n, uint32_t d,
-                                                   float *__restrict__ out)
+__global__ void __launch_bounds__(edm_tile_threads(RHO), edm_tile_min_ctas(RHO))
+    k_edm_tiled(Tiles tiles, const float *__restrict__ x, uint32_t n, uint32_t d, float *__restrict__ out)
 {
-    using Tile = EdmTile<RHO, KC, X2>;
+    using Tile = typename EdmTileFor<RHO, X2>::type;
     __shared__ __align__(16) float sm[Tile::SMEM_FLOATS];
     const uint64_t stride = P ? gridDim.x : tiles.units;
     for (uint64_t u = blockIdx.x; u < tiles.units; u += stride) {
@@ -28,14 +26,15 @@ template <class Tiles, int RHO, bool X2>
 td_status launch_tiles(const Tiles &t, bool P, const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st,
                        uint64_t *ctas)
 {
+    constexpr int NT = EdmTileFor<RHO, X2>::type::NT;
     if (t.units == 0) return TD_OK;
     if (P) {
         auto k = k_edm_tiled<Tiles, RHO, X2, true>;
-        const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, t.units);
-        k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, x, n, d, out);
+        const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), NT, 0, t.units);
+        k<<<dim3(static_cast<uint32_t>(g)), NT, 0, st>>>(t, x, n, d, out);
         *ctas += g;
     } else {
-        k_edm_tiled<Tiles, RHO, X2, false><<<dim3(static_cast<uint32_t>(t.units)), 256, 0, st>>>(t, x, n, d, out);
+        k_edm_tiled<Tiles, RHO, X2, false><<<dim3(static_cast<uint32_t>(t.units)), NT, 0, st>>>(t, x, n, d, out);
         *ctas += t.units;
     }
     return launch_status("td_edm tiled kernel");

@@ -1,13 +1,11 @@
 // td_edm_tile.cuh -- the register-tiled block body of the Euclidean distance map (Sec. IV of
 // arXiv:1308.1419), shared by td_edm (rho 64/128) and the batched distance map.
 //
-// One CTA of 256 threads computes one rho x rho block of the packed lower triangle.  The
+// One CTA computes one rho x rho block of the packed lower triangle.  The
 // block's rho row points and rho column points are staged in shared memory by asynchronous
 // copies, KC features at a time, feature-major and double-buffered (chunk c + 1 loads while
-// chunk c is consumed); each thread keeps a TM x TM register tile (TM = rho / 16) for rows
-// {tr + 16 a} and columns {tc + 16 b}, so every feature step is two 128-bit shared loads and
-// TM^2 subtract/FMA pairs.  The shared-memory slot of row r is (r mod 16) TM + floor(r / 16):
-// the TM rows a thread owns sit side by side.  With X2, two columns go through each packed
+// chunk c is consumed); each thread keeps a TM x TN register tile of partial sums, so every
+// feature step is a few 128-bit shared loads and TM TN subtract/FMA pairs.  With X2, two columns go through each packed
 // sub.rn.f32x2 / fma.rn.f32x2 (sm_100+), which round every lane like the scalar instructions.
 //
 // Summation order is the one of every EDM kernel in libtd: t = x_i[k] - x_j[k],
@@ -56,53 +54,66 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int RHO, int KC, bool X2>
+// TM x TN register tile per thread: NT = (RHO / TM) (RHO / TN) threads.  Thread (tr, tc) owns rows
+// tr + (RHO / TM) a, a < TM, and columns tc + (RHO / TN) b, b < TN; consecutive threads take
+// consecutive tc, so a warp reads consecutive 16-byte column granules (no bank conflicts) and,
+// when RHO / TN = 32, shares one tr (row values by broadcast) and stores 32 consecutive floats of
+// one packed row per instruction.
+template <int RHO, int KC, int TM, int TN, bool X2>
 struct EdmTile {
-    static constexpr int TM = RHO / 16;
+    static constexpr int RT = RHO / TM, CT = RHO / TN;  // row threads, column threads
+    static constexpr int NT = RT * CT;
     static constexpr int LD = RHO + 4;  // padded row of a feature plane, keeps 16-byte alignment
     static constexpr int STAGE_FLOATS = 2 * KC * LD;     // rows and columns of one feature chunk
     static constexpr int SMEM_FLOATS = 2 * STAGE_FLOATS;  // double-buffered
-    static_assert(TM % 4 == 0, "TM must be a multiple of 4");
+    static_assert(TM % 4 == 0 && TN % 4 == 0, "TM and TN must be multiples of 4");
 
-    // Slot of row (or column) r = t + 16 b (t = r mod 16, b = r / 16) in a feature plane: thread t
-    // reads its TM values as TM/4 16-byte granules t, t + 16, t + 32, ...; granule g holds
-    // b = 4 (g / 16) .. +3.  Consecutive threads read consecutive granules: no bank conflicts.
-    __device__ static __forceinline__ int slot(int r)
+    // Slot of row r = tr + RT a in the row plane: thread tr reads granules tr, tr + RT, ...;
+    // granule g holds a = 4 (g / RT) .. +3.  Same scheme with CT, b for columns.
+    __device__ static __forceinline__ int slot_row(int r)
     {
-        const int t = r & 15, b = r >> 4;
-        return (((b >> 2) << 4) + t) * 4 + (b & 3);
+        const int t = r % RT, a = r / RT;
+        return ((a >> 2) * RT + t) * 4 + (a & 3);
     }
+    __device__ static __forceinline__ int slot_col(int c)
+    {
+        const int t = c % CT, b = c / CT;
+        return ((b >> 2) * CT + t) * 4 + (b & 3);
+    }
+    static constexpr bool SAME_LAYOUT = TM == TN;  // a diagonal block may read columns from the row plane
 
     // Issues the asynchronous copies of features [k0, k0 + kc) of the block's rows and columns.
     __device__ static __forceinline__ void stage(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0,
                                                  uint32_t j0, bool diag, uint32_t k0, int kc, float *buf)
     {
         float *sA = buf, *sB = buf + KC * LD;
-        for (int e = threadIdx.x; e < RHO * kc; e += 256) {
+        const bool need_b = !(diag && SAME_LAYOUT);
+        for (int e = threadIdx.x; e < RHO * kc; e += NT) {
             const int r = e % RHO, kk = e / RHO;
             const uint32_t i = i0 + r, j = j0 + r, k = k0 + kk;
-            cp_async4(sA + kk * LD + slot(r), i < n ? x + uint64_t(i) * d + k : x, i < n ? 4u : 0u);
-            if (!diag) cp_async4(sB + kk * LD + slot(r), j < n ? x + uint64_t(j) * d + k : x, j < n ? 4u : 0u);
+            cp_async4(sA + kk * LD + slot_row(r), i < n ? x + uint64_t(i) * d + k : x, i < n ? 4u : 0u);
+            if (need_b) cp_async4(sB + kk * LD + slot_col(r), j < n ? x + uint64_t(j) * d + k : x, j < n ? 4u : 0u);
         }
         cp_async_commit();
     }
 
-    // sm: SMEM_FLOATS floats.  All 256 threads of the CTA call it together.
+    // sm: SMEM_FLOATS floats.  All NT threads of the CTA call it together.
     __device__ static void run(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
                                float *__restrict__ out, float *sm)
     {
-        const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+        const int tid = threadIdx.x, tr = tid / CT, tc = tid % CT;
         const bool diag = i0 == j0;
-        float acc[TM][TM];
-        unsigned long long acc2[TM][TM / 2];
+        const bool b_from_a = diag && SAME_LAYOUT;
+        float acc[TM][TN];
+        unsigned long long acc2[TM][TN / 2];
 #pragma unroll
         for (int a = 0; a < TM; ++a)
 #pragma unroll
-            for (int b = 0; b < TM; ++b) acc[a][b] = 0.0f;
+            for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
 #pragma unroll
         for (int a = 0; a < TM; ++a)
 #pragma unroll
-            for (int b = 0; b < TM / 2; ++b) acc2[a][b] = 0ull;
+            for (int b = 0; b < TN / 2; ++b) acc2[a][b] = 0ull;
 
         const uint32_t nchunks = (d + KC - 1) / KC;
         stage(x, n, d, i0, j0, diag, 0, d < uint32_t(KC) ? int(d) : KC, sm);
@@ -119,26 +130,29 @@ struct EdmTile {
             }
             __syncthreads();
             const float *sA = sm + (c & 1) * STAGE_FLOATS;
-            const float *B = diag ? sA : sA + KC * LD;
+            const float *B = b_from_a ? sA : sA + KC * LD;
 #pragma unroll 2
             for (int kk = 0; kk < kc; ++kk) {
-                float av[TM], bv[TM];
+                float av[TM], bv[TN];
 #pragma unroll
                 for (int h = 0; h < TM / 4; ++h) {
-                    const float4 va = *reinterpret_cast<const float4 *>(sA + kk * LD + (h * 16 + tr) * 4);
-                    const float4 vb = *reinterpret_cast<const float4 *>(B + kk * LD + (h * 16 + tc) * 4);
+                    const float4 va = *reinterpret_cast<const float4 *>(sA + kk * LD + (h * RT + tr) * 4);
                     av[4 * h] = va.x; av[4 * h + 1] = va.y; av[4 * h + 2] = va.z; av[4 * h + 3] = va.w;
+                }
+#pragma unroll
+                for (int h = 0; h < TN / 4; ++h) {
+                    const float4 vb = *reinterpret_cast<const float4 *>(B + kk * LD + (h * CT + tc) * 4);
                     bv[4 * h] = vb.x; bv[4 * h + 1] = vb.y; bv[4 * h + 2] = vb.z; bv[4 * h + 3] = vb.w;
                 }
                 if (X2) {
-                    unsigned long long b2[TM / 2];
+                    unsigned long long b2[TN / 2];
 #pragma unroll
-                    for (int q = 0; q < TM / 2; ++q) b2[q] = pack2(bv[2 * q], bv[2 * q + 1]);
+                    for (int q = 0; q < TN / 2; ++q) b2[q] = pack2(bv[2 * q], bv[2 * q + 1]);
 #pragma unroll
                     for (int a = 0; a < TM; ++a) {
                         const unsigned long long a2 = pack2(av[a], av[a]);
 #pragma unroll
-                        for (int q = 0; q < TM / 2; ++q) {
+                        for (int q = 0; q < TN / 2; ++q) {
                             const unsigned long long t = sub_f32x2(a2, b2[q]);
                             acc2[a][q] = fma_f32x2(t, t, acc2[a][q]);
                         }
@@ -147,7 +161,7 @@ struct EdmTile {
 #pragma unroll
                     for (int a = 0; a < TM; ++a)
 #pragma unroll
-                        for (int b = 0; b < TM; ++b) {
+                        for (int b = 0; b < TN; ++b) {
                             const float t = av[a] - bv[b];
                             acc[a][b] = fmaf(t, t, acc[a][b]);
                         }
@@ -159,22 +173,34 @@ struct EdmTile {
 #pragma unroll
             for (int a = 0; a < TM; ++a)
 #pragma unroll
-                for (int q = 0; q < TM / 2; ++q) unpack2(acc2[a][q], acc[a][2 * q], acc[a][2 * q + 1]);
+                for (int q = 0; q < TN / 2; ++q) unpack2(acc2[a][q], acc[a][2 * q], acc[a][2 * q + 1]);
         }
-        // Thread (tr, tc) owns rows i0 + tr + 16a and columns j0 + tc + 16b; for fixed (a, b)
-        // a warp writes two 64-byte runs of two packed rows.
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
-            const uint32_t i = i0 + tr + 16 * a;
+            const uint32_t i = i0 + tr + RT * a;
             if (i >= n) continue;
             float *row = out + tri(i);
 #pragma unroll
-            for (int b = 0; b < TM; ++b) {
-                const uint32_t j = j0 + tc + 16 * b;
+            for (int b = 0; b < TN; ++b) {
+                const uint32_t j = j0 + tc + CT * b;
                 if (j <= i) row[j] = sqrtf(acc[a][b]);
             }
         }
     }
+};
+
+// The block bodies used for each block side: rho = 64 -> 4 x 4 tiles, rho = 128 -> 8 x 8 tiles,
+// 256 threads each.
+__host__ __device__ constexpr int edm_tile_tm(int rho) { return rho / 16; }
+__host__ __device__ constexpr int edm_tile_tn(int rho) { return rho / 16; }
+__host__ __device__ constexpr int edm_tile_threads(int rho) { return (rho / edm_tile_tm(rho)) * (rho / edm_tile_tn(rho)); }
+// resident CTAs asked of the compiler (the 8 x 8 tile keeps its 128 registers: measured faster
+// than 8 x 4 tiles with twice the warps)
+__host__ __device__ constexpr int edm_tile_min_ctas(int rho) { return rho == 128 ? 2 : 4; }
+
+template <int RHO, bool X2>
+struct EdmTileFor {
+    using type = EdmTile<RHO, 16, edm_tile_tm(RHO), edm_tile_tn(RHO), X2>;
 };
 
 }  // namespace td

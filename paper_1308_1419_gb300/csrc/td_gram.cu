@@ -15,13 +15,13 @@
 //                            of the block's row and column points into a 4-stage ring;
 //                  warp 1    MMA issuer: tcgen05.mma (M = N = 128, K = 16) into one of two FP32 TMEM
 //                            accumulators, each ring stage released by tcgen05.commit;
-//                  warps 2-9 epilogue: read the accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
-//                            columns 64 ((w - 2) / 4) ..), form D^2, append the cancelling pairs to a
+//                  warps 2-17 epilogue: read the accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
+//                            columns 32 ((w - 2) / 4) ..), form D^2, append the cancelling pairs to a
 //                            global queue (one atomic per warp and 32 columns), take the square root
 //                            of the rest and write packed rows through a per-warp transpose, then
 //                            release the accumulator.
 //                The two accumulators let the next block's loads and MMAs run under the epilogue.
-//   k_gram_fix   recomputes the queued pairs in the direct form: one warp per 4 pairs, 16-byte loads,
+//   k_gram_fix   recomputes the queued pairs in the direct form: one warp per 2 pairs, 16-byte loads,
 //                lanes striding the features, partial sums combined in a fixed butterfly order.
 // If the queue is full, the epilogue recomputes the extra pairs itself.  Every mbarrier wait is
 // bounded; a timeout records an error code in the workspace status word and the roles wind down,
@@ -40,7 +40,7 @@ constexpr uint32_t BM = 128;           // block side (rows and columns)
 constexpr uint32_t BK = 64;            // features per BF16 TMA box (128 bytes)
 constexpr uint32_t BOX = BM * BK * 2;  // 16 KB
 constexpr uint32_t STAGES = 4;         // ring stages, one box of rows and one of columns each
-constexpr uint32_t EPI_WARPS = 8;
+constexpr uint32_t EPI_WARPS = 16;
 constexpr uint32_t THREADS = 32 * (2 + EPI_WARPS);
 constexpr uint32_t SLD = 33;           // padded row of the transpose stage
 constexpr uint32_t TMEM_COLS = 256;    // two 128-column FP32 accumulators
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ---------------- epilogue warps
-        const uint32_t ew = warp - 2, q = warp & 3, half = ew >> 2;
+        const uint32_t ew = warp - 2, q = warp & 3, chunk = ew >> 2;
         float *st = reinterpret_cast<float *>(sm + OFF_STAGE) + ew * 32 * SLD;
         uint64_t t = 0;
         for (uint64_t lam = blockIdx.x; lam < tiles; lam += gridDim.x, ++t) {
@@ -219,9 +219,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_after();
             const uint32_t rl = 32 * q + lane, i = bi * BM + rl;
             const float ni = i < n ? __ldg(norms + i) : 0.0f;
-#pragma unroll 1
-            for (uint32_t c = 0; c < 2; ++c) {
-                const uint32_t c0 = 64 * half + 32 * c;
+            {
+                const uint32_t c0 = 32 * chunk;
                 const uint32_t jl = bj * BM + c0 + lane;
                 const float njl = jl < n ? __ldg(norms + jl) : 0.0f;  // lane l holds column c0 + l's norm
                 float v[32];
@@ -277,30 +276,37 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
-// Direct FP32 recompute of the queued pairs: a warp takes 4 pairs at a time, lanes stride the
-// features 4 at a time (16-byte loads), and the per-lane partial sums are combined in a fixed
-// butterfly order.  d is a multiple of 4.
-__global__ void __launch_bounds__(256) k_gram_fix(const float *__restrict__ x, uint32_t d,
-                                                  const uint2 *__restrict__ queue, const uint32_t *__restrict__ status,
-                                                  uint64_t qcap, float *__restrict__ out)
+// Direct FP32 recompute of the queued pairs: a warp takes FIX_PAIRS pairs at a time, lanes stride
+// the features 4 at a time (16-byte loads, two iterations in flight), and the per-lane partial
+// sums are combined in a fixed butterfly order.  d is a multiple of 4.
+constexpr int FIX_PAIRS = 2;
+
+__global__ void __launch_bounds__(256, 4) k_gram_fix(const float *__restrict__ x, uint32_t d,
+                                                     const uint2 *__restrict__ queue,
+                                                     const uint32_t *__restrict__ status, uint64_t qcap,
+                                                     float *__restrict__ out)
 {
     const unsigned long long cnt = *reinterpret_cast<const unsigned long long *>(status + 2);
     const uint64_t total = cnt < qcap ? cnt : qcap;
     const uint32_t lane = threadIdx.x & 31, d4 = d / 4;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-    for (uint64_t e = (uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; e < total; e += warps * 4) {
-        uint2 pr[4];
-        float part[4];
+    for (uint64_t e = (uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * FIX_PAIRS; e < total;
+         e += warps * FIX_PAIRS) {
+        const float4 *xi[FIX_PAIRS], *xj[FIX_PAIRS];
+        uint2 pr[FIX_PAIRS];
+        float part[FIX_PAIRS];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < FIX_PAIRS; ++p) {
             pr[p] = e + p < total ? queue[e + p] : make_uint2(0u, 0u);
+            xi[p] = reinterpret_cast<const float4 *>(x + uint64_t(pr[p].x) * d);
+            xj[p] = reinterpret_cast<const float4 *>(x + uint64_t(pr[p].y) * d);
             part[p] = 0.0f;
         }
+#pragma unroll 2
         for (uint32_t k4 = lane; k4 < d4; k4 += 32) {
 #pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + uint64_t(pr[p].x) * d) + k4);
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(x + uint64_t(pr[p].y) * d) + k4);
+            for (int p = 0; p < FIX_PAIRS; ++p) {
+                const float4 a = __ldg(xi[p] + k4), b = __ldg(xj[p] + k4);
                 float t = a.x - b.x;
                 part[p] = fmaf(t, t, part[p]);
                 t = a.y - b.y;
@@ -312,7 +318,7 @@ __global__ void __launch_bounds__(256) k_gram_fix(const float *__restrict__ x, u
             }
         }
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < FIX_PAIRS; ++p) {
             float s2 = part[p];
             for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             if (lane == 0 && e + p < total) out[tri(pr[p].x) + pr[p].y] = sqrtf(s2);
@@ -395,7 +401,7 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
                                                                           status);
     s = launch_status("td_edm_gram kernel");
     if (s != TD_OK) return s;
-    k_gram_fix<<<dim3(8 * static_cast<uint32_t>(sm_count())), 256, 0, st>>>(x, d, queue, status, L.qcap, out);
+    k_gram_fix<<<dim3(4 * static_cast<uint32_t>(sm_count())), 256, 0, st>>>(x, d, queue, status, L.qcap, out);
     return launch_status("td_edm_gram recompute kernel");
 }
 
