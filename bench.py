@@ -30,6 +30,20 @@ STRATS = ["LTM", "BB", "UTM", "RB", "REC"]
 METRIC = "useful triangle pairs/s (g(lambda) probe sweep)"
 UNIT = "pairs/s"
 
+# DRAM traffic of the probe kernel (dram__bytes_read.sum + dram__bytes_write.sum), one ncu launch
+# per block side at N = 16384 (537 MB of output, above L2), in bytes per packed element.  The
+# kernel is write-only, so traffic scales with T(N); the N = 65536 figure is this times T(65536).
+# The numbers hold for the kernel sources whose digest is recorded here; once they change the
+# roofline line reports traffic as null until a new capture is taken.
+PROBE_SOURCES = ("td_probe.cu", "td_tiles.cuh", "td_device.cuh", "td_strategies.cuh")
+PROBE_TRAFFIC = {
+    "sources_sha256": None,
+    "bytes_per_pair": {},
+    "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+               "--clock-control none -k regex:k_probe_chunked -s 3 -c 1 "
+               "python bench.py --case probe:LTM:chunked:16384:<rho> --steps 1 --warmup 3",
+}
+
 
 def tri(n):
     return n * (n + 1) // 2
@@ -37,6 +51,22 @@ def tri(n):
 
 def sweep_pairs():
     return sum(tri(N) for N in SIZES for _ in RHOS)
+
+
+def probe_sources_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for name in PROBE_SOURCES:
+        with open(os.path.join(ROOT, "paper_1308_1419_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def headline_config(sched):
+    return {"workload": f"probe sweep: N in {{1024,4096,16384,65536}} x rho in {{8,16,32}}, g(lambda), {sched} schedule",
+            "useful_pairs_per_step": sweep_pairs(),
+            "l2": "inputs none; each step's three N=65536 launches write 8.6 GB each (> 129 MB L2), "
+                  "so L2 holds nothing of the previous step"}
 
 
 def load_peaks():
@@ -144,7 +174,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (no input; hash of (i, j))",
-        "config": {"workload": "probe sweep N in {1024,4096,16384,65536} x rho in {8,16,32}", "l2": "n/a (CPU)"},
+        "config": headline_config(args.sched),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{rows} whole rows of the N=65536 triangle per step"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -256,8 +286,13 @@ def run_ours(args):
         per_rho[r] = {"ms": t, "GBps": 4 * tri(65536) / (t / 1e3) / 1e9}
     dom = max(RHOS, key=lambda r: per_rho[r]["ms"])
     achieved = per_rho[dom]["GBps"]
+    traffic, traffic_note = None, "no ncu capture recorded for these kernel sources"
+    if (args.sched == "chunked" and PROBE_TRAFFIC["sources_sha256"] == probe_sources_digest()
+            and dom in PROBE_TRAFFIC["bytes_per_pair"]):
+        traffic = PROBE_TRAFFIC["bytes_per_pair"][dom] * tri(65536)
+        traffic_note = "ncu DRAM bytes at N=16384, scaled by T(65536)/T(16384) (write-only kernel)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"g(lambda) probe, {args.sched} schedule, rho={dom}, N=65536",
+                "traffic": traffic, "traffic_note": traffic_note, "kernel": f"g(lambda) probe, {args.sched} schedule, rho={dom}, N=65536",
                 "memset_write_GBps": memset_gbps,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs, copy)" if peak_kind == "measured" else "fallback",
                 "per_rho": {str(r): v for r, v in per_rho.items()},
@@ -308,9 +343,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic (no input array; each pair writes a hash of (i, j))",
-            "config": {"workload": f"probe sweep: N in {{1024,4096,16384,65536}} x rho in {{8,16,32}}, g(lambda), {args.sched}",
-                       "useful_pairs_per_step": sweep_pairs(),
-                       "l2": "outputs exceed L2 (8.6 GB per N=65536 launch)"},
+            "config": headline_config(args.sched),
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "roofline": roofline,
