@@ -403,7 +403,8 @@ def run_case(args):
             td.td_edm_gram(x, out, ws)
     elif kind == "batched":
         # batched:<how>:<rho>:<ctas_per_sm>, how = one (single persistent launch), graph (its graph
-        # replay), per (one td_edm launch per problem), tune (autotuned one launch)
+        # replay), per (one td_edm launch per problem), pergraph (those launches as one graph),
+        # tune (autotuned one launch)
         how, rho, cps = strategy, int(sched), int(parts[3])
         ns, ds, xh = synth.batched_problems()
         x = torch.from_numpy(xh).cuda()
@@ -427,6 +428,7 @@ def run_case(args):
             def call():
                 graph.replay()
         else:
+            # per: one td_edm launch per problem; pergraph: the same launches replayed as one graph
             xo = [0]
             oo = [0]
             for n, d in zip(ns, ds):
@@ -434,9 +436,19 @@ def run_case(args):
                 oo.append(oo[-1] + int(n) * (int(n) + 1) // 2)
             xs_l = [x[xo[p]: xo[p + 1]].view(int(ns[p]), int(ds[p])).clone() for p in range(len(ns))]
             outs = [torch.empty(oo[p + 1] - oo[p], dtype=torch.float32, device="cuda") for p in range(len(ns))]
-            def call():
+            def per_problem():
                 for p in range(len(ns)):
                     td.td_edm("LTM", "persistent", xs_l[p], rho, outs[p])
+            if how == "pergraph":
+                per_problem()
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    per_problem()
+                def call():
+                    graph.replay()
+            else:
+                call = per_problem
     else:
         raise SystemExit(f"unknown case {args.case}")
     for _ in range(args.warmup):

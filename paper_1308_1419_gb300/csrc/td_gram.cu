@@ -16,10 +16,10 @@
 //                  warp 1    MMA issuer: tcgen05.mma (M = N = 128, K = 16) into one of two FP32 TMEM
 //                            accumulators, each ring stage released by tcgen05.commit;
 //                  warps 2-17 epilogue: read the accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
-//                            columns 32 ((w - 2) / 4) ..), form D^2, append the cancelling pairs to a
-//                            global queue (one atomic per warp and 32 columns), take the square root
-//                            of the rest and write packed rows through a per-warp transpose, then
-//                            release the accumulator.
+//                            columns 32 ((w - 2) / 4) ..) and release it at once, form D^2, append
+//                            the cancelling pairs to a global queue (one atomic per warp and 32
+//                            columns), take the square root and write packed rows through a
+//                            per-warp transpose in shared memory.
 //                The two accumulators let the next block's loads and MMAs run under the epilogue.
 //   k_gram_fix   recomputes the queued pairs in the direct form: one warp per 2 pairs, 16-byte loads,
 //                lanes striding the features, partial sums combined in a fixed butterfly order.
@@ -42,7 +42,7 @@ constexpr uint32_t BOX = BM * BK * 2;  // 16 KB
 constexpr uint32_t STAGES = 4;         // ring stages, one box of rows and one of columns each
 constexpr uint32_t EPI_WARPS = 16;
 constexpr uint32_t THREADS = 32 * (2 + EPI_WARPS);
-constexpr uint32_t SLD = 33;           // padded row of the transpose stage
+constexpr uint32_t SLD = 36;           // padded row of the transpose stage (16-byte rows)
 constexpr uint32_t TMEM_COLS = 256;    // two 128-column FP32 accumulators
 constexpr float kCancel = 1e-2f;       // recompute when D^2 < kCancel (|x_i|^2 + |x_j|^2)
 
@@ -63,12 +63,17 @@ __device__ __forceinline__ float sqrt_approx(float v)
     return r;
 }
 
-// BF16 copy of the points and FP32 squared norms; one warp per point.
-__global__ void __launch_bounds__(256) k_gram_prep(const float *__restrict__ x, uint32_t n, uint32_t d,
-                                                   __nv_bfloat16 *__restrict__ xb, float *__restrict__ norms)
+// BF16 copy of the points and FP32 squared norms; one warp per point.  The norms are padded
+// with zeros up to npad (a whole number of blocks), so the epilogue reads them unchecked.
+__global__ void __launch_bounds__(256) k_gram_prep(const float *__restrict__ x, uint32_t n, uint32_t npad,
+                                                   uint32_t d, __nv_bfloat16 *__restrict__ xb,
+                                                   float *__restrict__ norms)
 {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= n) return;
+    if (warp >= n) {
+        if (warp < npad && lane == 0) norms[warp] = 0.0f;
+        return;
+    }
     const float *xi = x + uint64_t(warp) * d;
     __nv_bfloat16 *bi = xb + uint64_t(warp) * d;
     float s = 0.0f;
@@ -203,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
     } else {
         // ---------------- epilogue warps
-        const uint32_t ew = warp - 2, q = warp & 3, chunk = ew >> 2;
+        const uint32_t ew = warp - 2, q = warp & 3, c0 = 32 * (ew >> 2);
         float *st = reinterpret_cast<float *>(sm + OFF_STAGE) + ew * 32 * SLD;
         uint64_t t = 0;
         for (uint64_t lam = blockIdx.x; lam < tiles; lam += gridDim.x, ++t) {
@@ -217,24 +222,44 @@ __global__ void __launch_bounds__(THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t rl = 32 * q + lane, i = bi * BM + rl;
-            const float ni = i < n ? __ldg(norms + i) : 0.0f;
-            {
-                const uint32_t c0 = 32 * chunk;
-                const uint32_t jl = bj * BM + c0 + lane;
-                const float njl = jl < n ? __ldg(norms + jl) : 0.0f;  // lane l holds column c0 + l's norm
-                float v[32];
-                tmem_ld_32x32b_x32(tmem + a * BM + ((32 * q) << 16) + c0, v);
-                uint32_t mask = 0;
+            // this warp's 32 x 32 chunk: rows i0 + lane (TMEM lanes 32 q ..), columns jb + cc
+            const uint32_t i0 = bi * BM + 32 * q, i = i0 + lane, jb = bj * BM + c0;
+            // interior: every row below n and every column left of every row (then also below n)
+            const bool interior = bi > bj && i0 + 32 <= n;
+            float v[32];
+            tmem_ld_32x32b_x32(tmem + a * BM + ((32 * q) << 16) + c0, v);
+            // the accumulator is in registers: hand it back to the MMA warp before the arithmetic
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(a));
+            // D^2 = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j> and the cancellation test; the column norms
+            // arrive as broadcast 16-byte loads (the norms are zero-padded to whole blocks).  The
+            // sign of d2 - kCancel s2 is shifted into `neg` (column cc at bit 31 - cc).  A pair
+            // with d2 < 0 always cancels, so the NaN its square root gives is rewritten later.
+            const float ni = __ldg(norms + i);
+            const float4 *nj4 = reinterpret_cast<const float4 *>(norms + jb);
+            uint32_t neg = 0;
 #pragma unroll
-                for (uint32_t cc = 0; cc < 32; ++cc) {
-                    const uint32_t j = bj * BM + c0 + cc;
-                    const float s2 = ni + __shfl_sync(0xffffffffu, njl, cc);
-                    const float d2 = fmaf(-2.0f, v[cc], s2);
-                    const bool cancel = d2 < kCancel * s2;
-                    if (cancel && i < n && j <= i) mask |= 1u << cc;
-                    st[lane * SLD + cc] = cancel ? 0.0f : sqrt_approx(d2);
+            for (uint32_t c4 = 0; c4 < 8; ++c4) {
+                const float4 nq = __ldg(nj4 + c4);
+                const float nj[4] = {nq.x, nq.y, nq.z, nq.w};
+                float w[4];
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k) {
+                    const float s2 = ni + nj[k];
+                    const float d2 = fmaf(-2.0f, v[4 * c4 + k], s2);
+                    neg = __funnelshift_l(__float_as_uint(fmaf(-kCancel, s2, d2)), neg, 1);
+                    w[k] = sqrt_approx(d2);
                 }
+                *reinterpret_cast<float4 *>(st + lane * SLD + 4 * c4) = make_float4(w[0], w[1], w[2], w[3]);
+            }
+            uint32_t mask = __brev(neg);  // bit cc: pair (i, jb + cc) cancels
+            if (!interior) {  // keep pairs with i < n and j <= i (then j < n too)
+                const uint32_t lim = i < n ? i + 1 : 0u;
+                const uint32_t nv = lim > jb ? min(lim - jb, 32u) : 0u;
+                mask &= nv >= 32u ? 0xffffffffu : ((1u << nv) - 1u);
+            }
+            if (__any_sync(0xffffffffu, mask != 0)) {
                 // append this warp's cancelling pairs with one atomic: an exclusive scan of the
                 // per-lane counts gives each lane its slots
                 const uint32_t cnt = __popc(mask);
@@ -247,28 +272,34 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
                 pre -= cnt;
                 unsigned long long slot0 = 0;
-                if (total) {
-                    if (lane == 31) slot0 = atomicAdd(qcount, (unsigned long long)total);
-                    slot0 = __shfl_sync(0xffffffffu, slot0, 31);
-                }
+                if (lane == 31) slot0 = atomicAdd(qcount, (unsigned long long)total);
+                slot0 = __shfl_sync(0xffffffffu, slot0, 31);
                 uint64_t slot = slot0 + pre;
                 for (uint32_t m = mask; m; m &= m - 1, ++slot) {
-                    const uint32_t cc = __ffs(m) - 1, j = bj * BM + c0 + cc;
+                    const uint32_t cc = __ffs(m) - 1, j = jb + cc;
                     if (slot < qcap) queue[slot] = make_uint2(i, j);
                     else st[lane * SLD + cc] = direct_distance(x, d, i, j);  // queue full: recompute here
                 }
-                __syncwarp();
-                const uint32_t j2 = bj * BM + c0 + lane;
+            }
+            __syncwarp();
+            // transposed write-out: row i0 + rr, lane = column, 128 contiguous bytes per row
+            const uint32_t jl = jb + lane;
+            if (interior) {
+                float *p = out + tri(i0) + jl;
+                uint32_t step = i0 + 1;  // T(r + 1) - T(r) = r + 1
+#pragma unroll 8
+                for (uint32_t rr = 0; rr < 32; ++rr, ++step) {
+                    *p = st[rr * SLD + lane];
+                    p += step;
+                }
+            } else {
 #pragma unroll 4
                 for (uint32_t rr = 0; rr < 32; ++rr) {
-                    const uint32_t i2 = bi * BM + 32 * q + rr;
-                    if (i2 < n && j2 <= i2) out[tri(i2) + j2] = st[rr * SLD + lane];
+                    const uint32_t i2 = i0 + rr;
+                    if (i2 < n && jl <= i2) out[tri(i2) + jl] = st[rr * SLD + lane];
                 }
-                __syncwarp();
             }
-            tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty_bar(a));
         }
     }
     tc_fence_before();
@@ -351,12 +382,13 @@ struct GramLayout {
     uint64_t qcap;
 };
 
-// status (256 B) | norms (n floats) | BF16 points | queue of cancelling pairs (qcap x 8 B)
+// status (256 B) | norms (n floats, zero-padded to whole blocks) | BF16 points | queue of cancelling pairs (qcap x 8 B)
 GramLayout gram_layout(uint32_t n, uint32_t d)
 {
     GramLayout L;
     L.norms = 256;
-    L.xb = (L.norms + size_t(n) * 4 + 1023) & ~size_t(1023);
+    const size_t npad = size_t((n + BM - 1) / BM) * BM;
+    L.xb = (L.norms + npad * 4 + 1023) & ~size_t(1023);
     L.queue = (L.xb + size_t(n) * d * 2 + 1023) & ~size_t(1023);
     L.qcap = tri(n) / 32 + 65536;  // twice the 1/64 fraction of clustered data, plus slack
     L.total = L.queue + L.qcap * 8;
@@ -379,7 +411,8 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     if (!enc) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     td_status s = cuda_status(cudaMemsetAsync(status, 0, 16, st), "td_edm_gram status reset");
     if (s != TD_OK) return s;
-    k_gram_prep<<<(n + 7) / 8, 256, 0, st>>>(x, n, d, xb, norms);
+    const uint32_t npad = (n + BM - 1) / BM * BM;
+    k_gram_prep<<<(npad + 7) / 8, 256, 0, st>>>(x, n, npad, d, xb, norms);
     s = launch_status("td_edm_gram prep kernel");
     if (s != TD_OK) return s;
     CUtensorMap tmap;
