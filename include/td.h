@@ -81,7 +81,12 @@ typedef enum {
      * (sub.rn.f32x2 / fma.rn.f32x2); 0 (default): scalar FP32, measured no slower on GB300.
      * Both round identically, so the output does not depend on it. */
     TD_OPT_EDM_F32X2 = 0,
-    TD_OPT_COUNT = 1
+    /* Strip width of the CHUNKED probe schedule: the elements of one packed row a warp writes per
+     * strip of consecutive blocks.  0 (default): chosen per launch from its size (wider strips
+     * write longer contiguous runs; narrower ones balance better when there are few blocks);
+     * otherwise a power of two in [128, 8192].  Output does not depend on it. */
+    TD_OPT_PROBE_STRIP = 1,
+    TD_OPT_COUNT = 2
 } td_option;
 
 /* ------------------------------------------------------------------ host-only helpers */
@@ -92,7 +97,8 @@ int td_version(void);
 /* Message of the last failed call on this thread ("" if none).  Owned by the library. */
 const char *td_last_error(void);
 
-/* Sets / reads a library option.  Unknown option: TD_ERR_INVALID_ARG (td_get_option: 0). */
+/* Sets / reads a library option.  Unknown option or a value outside the option's range:
+ * TD_ERR_INVALID_ARG, option unchanged (td_get_option of an unknown option: 0). */
 td_status td_set_option(td_option opt, int value);
 int td_get_option(td_option opt);
 

@@ -199,6 +199,8 @@ td_status td_set_option(td_option opt, int value)
 {
     g_err[0] = 0;
     if (opt < 0 || opt >= TD_OPT_COUNT) return fail(TD_ERR_INVALID_ARG, "unknown option %d", int(opt));
+    if (opt == TD_OPT_PROBE_STRIP && value != 0 && (value < 128 || value > 8192 || (value & (value - 1)) != 0))
+        return fail(TD_ERR_INVALID_ARG, "probe strip width must be 0 or a power of two in [128, 8192] (got %d)", value);
     g_options[opt] = value;
     return TD_OK;
 }

@@ -26,13 +26,14 @@ struct CoverBody {
 };
 
 // ---------------------------------------------------------------- chunked probe (block strategies)
-// Persistent warps walk the launch space in strips of S = 256 / rho consecutive units.  Units
+// Persistent warps walk the launch space in strips of S = W / rho consecutive units (W, the strip
+// width in elements, a power of two >= 128 chosen per launch).  Units
 // that continue one block row -- blocks (bi, bj), (bi, bj+1), ... -- cover, in each element row
 // i of that block row, one contiguous flat range [s, e) of the packed output (s = T(i) + bj rho),
-// at most 256 elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
+// at most W elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
 // and chunk c is written by the block row range holding its first element 4c: the blocks of
 // every block strategy cover each element exactly once, so each chunk has exactly one writer.
-// All 32 lanes of a warp work on the same element row, lane l on chunks l and l + 32 of [s, e),
+// All 32 lanes of a warp work on the same element row, lane l on chunks l, l + 32, ... of [s, e),
 // so one store instruction writes up to 512 contiguous bytes; the stores are streaming
 // (st.global.cs), since every line is written once and never read back by the kernel.  A chunk that runs past e continues in
 // the same packed row or, at a row end, into the first elements of the next row(s); the probe
@@ -56,12 +57,9 @@ __device__ __forceinline__ uint4 probe4(uint32_t key)
                       splitmix32_mulshift(key + 3));
 }
 
-constexpr uint32_t kStripElems = 256;  // elements of one packed row a strip covers (2 chunks per lane)
-
 template <class Tiles, int RHO>
-__global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t *__restrict__ out)
+__global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t S, uint32_t *__restrict__ out)
 {
-    constexpr uint32_t S = kStripElems / RHO;  // units per strip
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
     const uint64_t strips = (tiles.units + S - 1) / S;
@@ -82,10 +80,8 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
                 uint32_t *row = out + ti;
                 // first row-local j >= jlo whose flat index T(i) + j is a multiple of 4
                 const uint32_t c0 = jlo + ((4u - ((static_cast<uint32_t>(ti) + jlo) & 3u)) & 3u);
-#pragma unroll
-                for (uint32_t c = 0; c < kStripElems / 128; ++c) {
-                    const uint32_t j = c0 + 4 * (lane + 32 * c);
-                    if (j >= jhi) break;
+#pragma unroll 2
+                for (uint32_t j = c0 + 4 * lane; j < jhi; j += 128) {
                     if (j + 3 <= i) {
                         __stcs(reinterpret_cast<uint4 *>(row + j), probe4(i * N + j));
                     } else {  // the chunk runs past the end of row i into the next row(s)
@@ -107,15 +103,31 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
     }
 }
 
+// Strip width: longer contiguous row segments per warp raise the write bandwidth at large N
+// (more of each DRAM page is written by one warp), but fewer strips balance worse over the
+// resident warps.  Default: the widest power of two in [256, kStripMax] that still leaves
+// kStripsPerWarp strips per resident warp; the library option overrides it.
+constexpr uint32_t kStripMin = 256, kStripMax = 2048, kStripsPerWarp = 4;
+
+uint32_t strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps)
+{
+    const int forced = option(TD_OPT_PROBE_STRIP);
+    if (forced > 0) return uint32_t(forced) < rho ? rho : uint32_t(forced);
+    uint32_t w = kStripMin;
+    while (w < kStripMax && units * rho / (2 * w) >= kStripsPerWarp * resident_warps) w *= 2;
+    return w < rho ? rho : w;
+}
+
 template <class Tiles, int RHO>
 td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
 {
     if (t.units == 0) return TD_OK;
-    constexpr uint32_t S = kStripElems / RHO;
-    const uint64_t strips = (t.units + S - 1) / S;
     auto k = k_probe_chunked<Tiles, RHO>;
+    const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, ~0ull) * 8;
+    const uint32_t S = strip_width(t.units, RHO, resident) / RHO;
+    const uint64_t strips = (t.units + S - 1) / S;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (strips + 7) / 8);
-    k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, out);
+    k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, S, out);
     *ctas += g;
     return launch_status("td probe chunked kernel");
 }

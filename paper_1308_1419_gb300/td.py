@@ -118,7 +118,7 @@ def td_version() -> int:
     return int(_c_version())
 
 
-OPTIONS = {"edm_f32x2": 0}
+OPTIONS = {"edm_f32x2": 0, "probe_strip": 1}
 
 
 def td_set_option(opt, value: int):

@@ -79,6 +79,17 @@ def test_argument_errors_return_before_launch():
     assert td._c_ltm_check(2**50, 10, 256, None) == 2
 
 
+def test_options_validated():
+    assert td.td_get_option("probe_strip") == 0                              # chosen per launch
+    for bad in (-1, 1, 64, 300, 16384):
+        assert td._c_set_option(1, bad) == 1 and "strip" in td._c_last_error().decode()
+        assert td.td_get_option("probe_strip") == 0                          # unchanged
+    td.td_set_option("probe_strip", 1024)
+    assert td.td_get_option("probe_strip") == 1024
+    td.td_set_option("probe_strip", 0)
+    assert td._c_set_option(7, 0) == 1 and td.td_get_option(7) == 0          # unknown option
+
+
 def test_oracle_not_imported_by_product():
     import glob
     pkg = os.path.dirname(td.__file__)
