@@ -141,10 +141,15 @@ td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho
  * correctly rounded sqrt -- the same order in every kernel, so every strategy, schedule and
  * rho gives bit-identical output.  x: device, float[n][d] row-major, 16-byte aligned;
  * out: device, float[T(n)], 16-byte aligned.  d >= 1.
- * rho in {8, 16, 32}: rho x rho threads per block, one element per thread, every strategy
- *   (the paper's EDM kernel).
- * rho in {64, 128}: one 256-thread CTA per rho x rho block with shared-memory coordinate
- *   tiles and register tiles, for large d; TD_MAP_LTM, TD_MAP_BB and TD_MAP_REC only.
+ * rho in {8, 16, 32}, sched GRID or PERSISTENT: rho x rho threads per block, one element per
+ *   thread, every strategy (the paper's EDM kernel).
+ * rho in {8, 16, 32}, sched CHUNKED (TD_MAP_LTM, TD_MAP_BB, TD_MAP_REC; d <= 8, else
+ *   TD_ERR_UNSUPPORTED): the same blocks walked by warps in strips of consecutive blocks of a
+ *   block row, column points staged in shared memory, aligned 16-byte stores -- the form for
+ *   few features, where the map is store-bound.
+ * rho in {64, 128}, sched GRID or PERSISTENT: one 256-thread CTA per rho x rho block with
+ *   shared-memory coordinate tiles and register tiles, for large d; TD_MAP_LTM, TD_MAP_BB and
+ *   TD_MAP_REC only (CHUNKED: TD_ERR_UNSUPPORTED).
  * stats: host, may be NULL.  n = 0 is a no-op. */
 td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                  float *out, td_launch_stats *stats, void *stream);

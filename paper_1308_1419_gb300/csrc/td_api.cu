@@ -256,8 +256,13 @@ td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, ui
     if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
     uint64_t ctas = 0;
     const cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    st = rho <= 32 ? launch_edm_pair(m, sched, x, n, d, rho, out, p, cs, &ctas)
-                   : launch_edm_tiled(m, sched, x, n, d, rho, out, p, option(TD_OPT_EDM_F32X2) != 0, cs, &ctas);
+    if (sched == TD_SCHED_CHUNKED && rho > 32)
+        return fail(TD_ERR_UNSUPPORTED, "the chunked distance map needs rho 8, 16 or 32 (rho 64/128 is the tiled body)");
+    if (sched == TD_SCHED_CHUNKED)
+        st = launch_edm_chunked(m, x, n, d, rho, out, p, cs, &ctas);
+    else
+        st = rho <= 32 ? launch_edm_pair(m, sched, x, n, d, rho, out, p, cs, &ctas)
+                       : launch_edm_tiled(m, sched, x, n, d, rho, out, p, option(TD_OPT_EDM_F32X2) != 0, cs, &ctas);
     fill_stats(stats, p, ctas);
     return st;
 }

@@ -1,0 +1,202 @@
+// td_edm_chunked.cu -- the Euclidean distance map of Sec. IV of arXiv:1308.1419 for few features
+// (d <= 8) under the chunked schedule of the block strategies (g(lambda), BB, REC).  With few
+// features the map is store-bound, and one element per thread (td_edm_pair.cu) leaves the HBM
+// write rate far behind; this body stores aligned 16-byte chunks instead.
+//
+// Warps walk strips of S = W / rho consecutive units as the chunked probe does (td_probe.cu): a
+// run of consecutive blocks (bi, bj) .. (bi, bj + run - 1) of one block row covers, in each of
+// its rho element rows i, the contiguous packed range T(i) + [bj rho, min((bj + run) rho, i + 1)),
+// and an aligned 16-byte chunk of the packed output is written by the run holding its first
+// element.  Per run, the warp stages the column points x_j, j = bj rho .. bj rho + run rho + 3,
+// feature-major in its slice of shared memory.  Per element row it keeps x_i in registers and
+// computes 128 columns at a time, lane l taking columns c + l + 32 m (m < 4: conflict-free shared
+// reads); the 128 results go through a per-warp buffer so that lane l then stores the aligned
+// chunk c + 4l .. c + 4l + 3 with one 16-byte streaming store.  A chunk that runs past the end of
+// row i into the next row(s) is computed element by element from global memory (at most one
+// chunk per row).
+//
+// Summation order as in every EDM kernel of libtd: t = x_i[k] - x_j[k], s = fma(t, t, s) for
+// k = 0 .. d-1 from s = 0, then sqrtf -- bit-identical to td_edm_pair and the tiled kernels.
+#include "td_internal.h"
+#include "td_tiles.cuh"
+
+namespace td {
+namespace {
+
+constexpr uint32_t kWarps = 8, kMaxD = 8;
+constexpr uint32_t kPad = 132;  // staged floats per feature row beyond the strip width (multiple of 4)
+
+// Widest strip a warp's shared-memory slice holds: (d sl + 128) floats per warp, sl = W + kPad.
+constexpr uint32_t edm_chunk_wmax(uint32_t d) { return d <= 4 ? 512u : 256u; }
+constexpr size_t edm_chunk_smem(uint32_t d, uint32_t w) { return size_t(kWarps) * (d * (w + kPad) + 128) * 4; }
+
+template <int D>
+__device__ __forceinline__ float direct(const float *__restrict__ x, uint32_t d, uint32_t i, uint32_t j)
+{
+    const uint32_t dd = D ? D : d;
+    const float *a = x + uint64_t(i) * dd, *b = x + uint64_t(j) * dd;
+    float s = 0.0f;
+#pragma unroll
+    for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
+        if (D == 0 && k >= dd) break;
+        const float t = __ldg(a + k) - __ldg(b + k);
+        s = fmaf(t, t, s);
+    }
+    return sqrtf(s);
+}
+
+template <class Tiles, int RHO, int D>
+__global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uint32_t n, uint32_t S, uint32_t sl,
+                                                             const float *__restrict__ x, uint32_t d,
+                                                             float *__restrict__ out)
+{
+    extern __shared__ __align__(16) float esm[];
+    const uint32_t dd = D ? D : d;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *sx = esm + warp * (dd * sl + 128);  // dd feature rows of sl floats: column c of the run
+    float *sres = sx + dd * sl;                // results of the current 128 columns
+    const uint64_t warps = uint64_t(gridDim.x) * kWarps;
+    const uint64_t strips = (tiles.units + S - 1) / S;
+    for (uint64_t z = uint64_t(blockIdx.x) * kWarps + warp; z < strips; z += warps) {
+        const uint64_t uend = min(tiles.units, (z + 1) * S);
+        for (uint64_t u = z * S; u < uend;) {
+            uint32_t bi, bj;
+            const bool ok = tiles(u, bi, bj);
+            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(uend - u));
+            u += run;
+            if (!ok) continue;
+            const uint32_t jlo = bj * RHO, ncol = run * RHO + 4;
+            __syncwarp();  // the previous run's reads of the slice are done
+            for (uint32_t c = lane; c < ncol; c += 32) {
+                const uint32_t j = jlo + c;
+                const float *xj = x + uint64_t(j) * dd;
+#pragma unroll
+                for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
+                    if (D == 0 && k >= dd) break;
+                    sx[k * sl + c] = j < n ? __ldg(xj + k) : 0.0f;
+                }
+            }
+            __syncwarp();
+            for (uint32_t r = 0; r < uint32_t(RHO); ++r) {
+                const uint32_t i = bi * RHO + r;
+                if (i >= n) break;
+                const uint32_t jhi = min((bj + run) * RHO, i + 1);  // row-local end (exclusive)
+                const uint64_t ti = tri(i);
+                // first column >= jlo whose flat index T(i) + j is a multiple of 4
+                const uint32_t c0 = jlo + ((4u - ((static_cast<uint32_t>(ti) + jlo) & 3u)) & 3u);
+                float xi[D ? D : kMaxD];
+#pragma unroll
+                for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) xi[k] = (D || k < dd) ? __ldg(x + uint64_t(i) * dd + k) : 0.0f;
+                for (uint32_t jb = c0; jb < jhi; jb += 128) {
+#pragma unroll
+                    for (uint32_t m = 0; m < 4; ++m) {
+                        const uint32_t c = jb - jlo + lane + 32 * m;
+                        float s = 0.0f;
+#pragma unroll
+                        for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
+                            if (D == 0 && k >= dd) break;
+                            const float t = xi[k] - sx[k * sl + c];
+                            s = fmaf(t, t, s);
+                        }
+                        sres[lane + 32 * m] = sqrtf(s);
+                    }
+                    __syncwarp();
+                    const uint32_t j = jb + 4 * lane;
+                    if (j < jhi) {
+                        if (j + 3 <= i) {
+                            __stcs(reinterpret_cast<float4 *>(out + ti + j), *reinterpret_cast<const float4 *>(sres + 4 * lane));
+                        } else {  // the chunk runs past the end of row i into the next row(s)
+                            uint32_t ii = i;
+                            uint64_t tii = ti;
+                            for (uint32_t q = 0; q < 4; ++q) {
+                                const uint64_t P = ti + j + q;
+                                while (P > tii + ii) {
+                                    tii += ii + 1;
+                                    ++ii;
+                                }
+                                if (ii >= n) break;
+                                out[P] = direct<D>(x, d, ii, static_cast<uint32_t>(P - tii));
+                            }
+                        }
+                    }
+                    __syncwarp();  // sres is rewritten by the next column group
+                }
+            }
+        }
+    }
+}
+
+template <class Tiles, int RHO, int D>
+td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st,
+                       uint64_t *ctas)
+{
+    if (t.units == 0) return TD_OK;
+    auto k = k_edm_chunked<Tiles, RHO, D>;
+    const uint32_t wmax = edm_chunk_wmax(d);
+    const size_t smax = edm_chunk_smem(d, wmax);
+    td_status s = cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax)),
+                              "td_edm chunked shared memory attribute");
+    if (s != TD_OK) return s;
+    const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smax, ~0ull) * kWarps;
+    const uint32_t w = chunked_strip_width(t.units, RHO, resident, wmax, wmax);
+    const uint32_t S = w / RHO, sl = w + kPad;
+    const size_t smem = edm_chunk_smem(d, w);
+    const uint64_t strips = (t.units + S - 1) / S;
+    const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smem, (strips + kWarps - 1) / kWarps);
+    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, smem, st>>>(t, n, S, sl, x, d, out);
+    *ctas += g;
+    return launch_status("td_edm chunked kernel");
+}
+
+template <int RHO, int D>
+td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float *out, const Plan &p, cudaStream_t st,
+                     uint64_t *ctas)
+{
+    switch (m) {
+    case TD_MAP_LTM: return launch_tiles<tiles::Ltm, RHO, D>(tiles::Ltm{tri(p.nb)}, x, n, d, out, st, ctas);
+    case TD_MAP_BB:
+        return launch_tiles<tiles::Bb, RHO, D>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, x, n, d, out, st, ctas);
+    case TD_MAP_REC: {
+        for (uint32_t l = 1; l <= p.rec_k; ++l) {
+            const uint32_t sb = (n >> l) / RHO, gx = n / (2 * RHO);
+            const td_status s =
+                launch_tiles<tiles::RecLevel, RHO, D>(tiles::RecLevel{uint64_t(gx) * sb, sb, gx}, x, n, d, out, st, ctas);
+            if (s != TD_OK) return s;
+        }
+        const uint32_t mb = p.rec_m / RHO, gx = n / RHO;
+        return launch_tiles<tiles::RecDiag, RHO, D>(tiles::RecDiag{uint64_t(gx) * mb, mb, gx}, x, n, d, out, st, ctas);
+    }
+    default:
+        return fail(TD_ERR_UNSUPPORTED, "the chunked schedule serves the block strategies LTM, BB and REC");
+    }
+}
+
+template <int D>
+td_status launch_d(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out, const Plan &p,
+                   cudaStream_t st, uint64_t *ctas)
+{
+    switch (rho) {
+    case 8: return launch_rho<8, D>(m, x, n, d, out, p, st, ctas);
+    case 16: return launch_rho<16, D>(m, x, n, d, out, p, st, ctas);
+    case 32: return launch_rho<32, D>(m, x, n, d, out, p, st, ctas);
+    default: return fail(TD_ERR_INVALID_ARG, "the chunked distance map needs rho 8, 16 or 32 (got %u)", rho);
+    }
+}
+
+}  // namespace
+
+td_status launch_edm_chunked(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
+                             const Plan &p, cudaStream_t st, uint64_t *ctas)
+{
+    if (d == 0 || d > kMaxD)
+        return fail(TD_ERR_UNSUPPORTED, "the chunked distance map serves d <= %u (got %u); use rho 64/128", kMaxD, d);
+    switch (d) {
+    case 1: return launch_d<1>(m, x, n, d, rho, out, p, st, ctas);
+    case 2: return launch_d<2>(m, x, n, d, rho, out, p, st, ctas);
+    case 3: return launch_d<3>(m, x, n, d, rho, out, p, st, ctas);
+    case 4: return launch_d<4>(m, x, n, d, rho, out, p, st, ctas);
+    default: return launch_d<0>(m, x, n, d, rho, out, p, st, ctas);
+    }
+}
+
+}  // namespace td

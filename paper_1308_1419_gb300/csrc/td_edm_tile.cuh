@@ -1,12 +1,17 @@
 // td_edm_tile.cuh -- the register-tiled block body of the Euclidean distance map (Sec. IV of
 // arXiv:1308.1419), shared by td_edm (rho 64/128) and the batched distance map.
 //
-// One CTA computes one rho x rho block of the packed lower triangle.  The
-// block's rho row points and rho column points are staged in shared memory by asynchronous
-// copies, KC features at a time, feature-major and double-buffered (chunk c + 1 loads while
-// chunk c is consumed); each thread keeps a TM x TN register tile of partial sums, so every
-// feature step is a few 128-bit shared loads and TM TN subtract/FMA pairs.  With X2, two columns go through each packed
-// sub.rn.f32x2 / fma.rn.f32x2 (sm_100+), which round every lane like the scalar instructions.
+// One CTA computes one rho x rho block of the packed lower triangle.  The block's rho row points
+// and rho column points are staged in shared memory by asynchronous copies, KC features at a
+// time, double-buffered (chunk c + 1 loads while chunk c is consumed); each thread keeps a
+// TM x TN register tile of partial sums.  Two staging layouts:
+//   point-major (d a multiple of 4 and 16-byte aligned points): 16-byte copies of 4 features of
+//     one point, rows padded to KC + 4 floats; a thread reads 4 features of a point per 128-bit
+//     shared load and applies them to its tile in feature order;
+//   feature-major (any d, and the X2 form): 4-byte copies into one plane per feature, a feature
+//     step being a few 128-bit shared loads of TM row and TN column values.
+// With X2, two columns go through each packed sub.rn.f32x2 / fma.rn.f32x2 (sm_100+), which
+// round every lane like the scalar instructions.
 //
 // Summation order is the one of every EDM kernel in libtd: t = x_i[k] - x_j[k],
 // s = fma(t, t, s) for k = 0 .. d-1 from s = 0, then sqrtf -- so the output is bit-identical to
@@ -50,6 +55,13 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, uint32_t
                  "l"(src), "r"(src_bytes)
                  : "memory");
 }
+// 16-byte asynchronous global -> shared copy (L2 only); src_bytes = 0 writes zeros without reading.
+__device__ __forceinline__ void cp_async16(float *dst, const float *src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -64,9 +76,13 @@ struct EdmTile {
     static constexpr int RT = RHO / TM, CT = RHO / TN;  // row threads, column threads
     static constexpr int NT = RT * CT;
     static constexpr int LD = RHO + 4;  // padded row of a feature plane, keeps 16-byte alignment
-    static constexpr int STAGE_FLOATS = 2 * KC * LD;     // rows and columns of one feature chunk
+    static constexpr int PLD = KC + 4;  // padded point row of the point-major layout (conflict-free reads)
+    static constexpr int FM_STAGE = 2 * KC * LD;   // feature-major rows and columns of one chunk
+    static constexpr int PM_STAGE = 2 * RHO * PLD;  // point-major rows and columns of one chunk
+    static constexpr int STAGE_FLOATS = FM_STAGE > PM_STAGE ? FM_STAGE : PM_STAGE;
     static constexpr int SMEM_FLOATS = 2 * STAGE_FLOATS;  // double-buffered
     static_assert(TM % 4 == 0 && TN % 4 == 0, "TM and TN must be multiples of 4");
+    static_assert(KC % 4 == 0 && (PLD * 4) % 16 == 0, "point-major rows must stay 16-byte aligned");
 
     // Slot of row r = tr + RT a in the row plane: thread tr reads granules tr, tr + RT, ...;
     // granule g holds a = 4 (g / RT) .. +3.  Same scheme with CT, b for columns.
@@ -97,9 +113,105 @@ struct EdmTile {
         cp_async_commit();
     }
 
+    // Point-major staging of features [k0, k0 + kc) (kc a multiple of 4): point r's 4-feature group
+    // f goes to row r, floats 4f .. 4f + 3, of the row (A) or column (B) plane.
+    __device__ static __forceinline__ void stage_pm(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0,
+                                                    uint32_t j0, bool diag, uint32_t k0, int kc, float *buf)
+    {
+        float *sA = buf, *sB = buf + RHO * PLD;
+        for (int e = threadIdx.x; e < RHO * (KC / 4); e += NT) {
+            const int r = e / (KC / 4), f = e % (KC / 4);
+            if (4 * f >= kc) continue;
+            const uint32_t i = i0 + r, j = j0 + r, k = k0 + 4 * f;
+            cp_async16(sA + r * PLD + 4 * f, i < n ? x + uint64_t(i) * d + k : x, i < n ? 16u : 0u);
+            if (!diag) cp_async16(sB + r * PLD + 4 * f, j < n ? x + uint64_t(j) * d + k : x, j < n ? 16u : 0u);
+        }
+        cp_async_commit();
+    }
+
+    // Point-major form of run(): the same sums, each accumulator taking features in order.
+    __device__ static void run_pm(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
+                                  float *__restrict__ out, float *sm)
+    {
+        const int tid = threadIdx.x, tr = tid / CT, tc = tid % CT;
+        const bool diag = i0 == j0;
+        float acc[TM][TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
+        const uint32_t nchunks = (d + KC - 1) / KC;
+        stage_pm(x, n, d, i0, j0, diag, 0, d < uint32_t(KC) ? int(d) : KC, sm);
+        for (uint32_t c = 0; c < nchunks; ++c) {
+            const uint32_t k0 = c * KC;
+            const int kc = d - k0 < uint32_t(KC) ? int(d - k0) : KC;
+            if (c + 1 < nchunks) {
+                const uint32_t k1 = k0 + KC;
+                stage_pm(x, n, d, i0, j0, diag, k1, d - k1 < uint32_t(KC) ? int(d - k1) : KC,
+                         sm + ((c + 1) & 1) * STAGE_FLOATS);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncthreads();
+            const float *A = sm + (c & 1) * STAGE_FLOATS;
+            const float *B = diag ? A : A + RHO * PLD;
+            for (int kk = 0; kk < kc; kk += 4) {
+                float4 av[TM];
+#pragma unroll
+                for (int a = 0; a < TM; ++a) av[a] = *reinterpret_cast<const float4 *>(A + (tr + RT * a) * PLD + kk);
+#pragma unroll
+                for (int b = 0; b < TN; ++b) {
+                    const float4 bv = *reinterpret_cast<const float4 *>(B + (tc + CT * b) * PLD + kk);
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) {
+                        float t = av[a].x - bv.x;
+                        acc[a][b] = fmaf(t, t, acc[a][b]);
+                        t = av[a].y - bv.y;
+                        acc[a][b] = fmaf(t, t, acc[a][b]);
+                        t = av[a].z - bv.z;
+                        acc[a][b] = fmaf(t, t, acc[a][b]);
+                        t = av[a].w - bv.w;
+                        acc[a][b] = fmaf(t, t, acc[a][b]);
+                    }
+                }
+            }
+            __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
+        }
+        store(n, i0, j0, out, acc);
+    }
+
+    __device__ static __forceinline__ void store(uint32_t n, uint32_t i0, uint32_t j0, float *__restrict__ out,
+                                                 const float (&acc)[TM][TN])
+    {
+        const int tid = threadIdx.x, tr = tid / CT, tc = tid % CT;
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+            const uint32_t i = i0 + tr + RT * a;
+            if (i >= n) continue;
+            float *row = out + tri(i);
+#pragma unroll
+            for (int b = 0; b < TN; ++b) {
+                const uint32_t j = j0 + tc + CT * b;
+                if (j <= i) row[j] = sqrtf(acc[a][b]);
+            }
+        }
+    }
+
     // sm: SMEM_FLOATS floats.  All NT threads of the CTA call it together.
     __device__ static void run(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
                                float *__restrict__ out, float *sm)
+    {
+        if (!X2 && d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+            run_pm(x, n, d, i0, j0, out, sm);
+            return;
+        }
+        run_fm(x, n, d, i0, j0, out, sm);
+    }
+
+    // Feature-major form (any d).
+    __device__ static void run_fm(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
+                                  float *__restrict__ out, float *sm)
     {
         const int tid = threadIdx.x, tr = tid / CT, tc = tid % CT;
         const bool diag = i0 == j0;
@@ -175,17 +287,7 @@ struct EdmTile {
 #pragma unroll
                 for (int q = 0; q < TN / 2; ++q) unpack2(acc2[a][q], acc[a][2 * q], acc[a][2 * q + 1]);
         }
-#pragma unroll
-        for (int a = 0; a < TM; ++a) {
-            const uint32_t i = i0 + tr + RT * a;
-            if (i >= n) continue;
-            float *row = out + tri(i);
-#pragma unroll
-            for (int b = 0; b < TN; ++b) {
-                const uint32_t j = j0 + tc + CT * b;
-                if (j <= i) row[j] = sqrtf(acc[a][b]);
-            }
-        }
+        store(n, i0, j0, out, acc);
     }
 };
 

@@ -33,6 +33,12 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
 // Launchers (stream-ordered, no synchronisation).
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
                        bool cover, const Plan &p, cudaStream_t st, uint64_t *ctas);
+// Strip width (elements of one packed row) of the chunked schedule: the widest power of two in
+// [256, wauto] leaving at least four strips per resident warp, or the TD_OPT_PROBE_STRIP value
+// (capped at wlimit); never below rho.
+uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit);
+td_status launch_edm_chunked(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
+                             const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_pair(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                           float *out, const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,

@@ -105,18 +105,10 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
 
 // Strip width: longer contiguous row segments per warp raise the write bandwidth at large N
 // (more of each DRAM page is written by one warp), but fewer strips balance worse over the
-// resident warps.  Default: the widest power of two in [256, kStripMax] that still leaves
-// kStripsPerWarp strips per resident warp; the library option overrides it.
-constexpr uint32_t kStripMin = 256, kStripMax = 2048, kStripsPerWarp = 4;
+// resident warps.  Default: the widest power of two in [256, kStripMax] that still leaves four
+// strips per resident warp (chunked_strip_width); the library option overrides it.
+constexpr uint32_t kStripMax = 2048;
 
-uint32_t strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps)
-{
-    const int forced = option(TD_OPT_PROBE_STRIP);
-    if (forced > 0) return uint32_t(forced) < rho ? rho : uint32_t(forced);
-    uint32_t w = kStripMin;
-    while (w < kStripMax && units * rho / (2 * w) >= kStripsPerWarp * resident_warps) w *= 2;
-    return w < rho ? rho : w;
-}
 
 template <class Tiles, int RHO>
 td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
@@ -124,7 +116,7 @@ td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaSt
     if (t.units == 0) return TD_OK;
     auto k = k_probe_chunked<Tiles, RHO>;
     const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, ~0ull) * 8;
-    const uint32_t S = strip_width(t.units, RHO, resident) / RHO;
+    const uint32_t S = chunked_strip_width(t.units, RHO, resident, kStripMax, 8192) / RHO;
     const uint64_t strips = (t.units + S - 1) / S;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (strips + 7) / 8);
     k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, S, out);
@@ -202,6 +194,18 @@ __global__ void k_ltm_check(uint64_t lam0, uint64_t count, unsigned long long *r
 }
 
 }  // namespace
+
+uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit)
+{
+    const int forced = option(TD_OPT_PROBE_STRIP);
+    uint32_t w = 256;
+    if (forced > 0) {
+        w = uint32_t(forced) < wlimit ? uint32_t(forced) : wlimit;
+    } else {
+        while (w < wauto && units * rho / (2 * w) >= 4 * resident_warps) w *= 2;
+    }
+    return w < rho ? rho : w;
+}
 
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out, bool cover,
                        const Plan &p, cudaStream_t st, uint64_t *ctas)

@@ -57,7 +57,7 @@ def test_plain_edm_config():
     assert np.all(ref[diag] == 0.0)
 
 
-@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 16, 64])
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 16, 36, 64, 100])
 def test_edm_ragged_all_kernels(d):
     for n in [1, 2, 17, 64, 100, 257, 640]:
         xh = synth.uniform_points(n, d, 1000 + n + d)
@@ -68,7 +68,8 @@ def test_edm_ragged_all_kernels(d):
             for mapping in STRATS:
                 if not _cases(mapping, rho, n):
                     continue
-                for sched in ("grid", "persistent"):
+                chunked = rho <= 32 and d <= 8 and mapping in ("LTM", "BB", "REC")
+                for sched in ("grid", "persistent") + (("chunked",) if chunked else ()):
                     got, _ = _edm(mapping, sched, x, rho)
                     _check_rel(got, want, (n, d, rho, mapping, sched))
                     if ref is None:
@@ -126,8 +127,37 @@ def test_edm_large_n_sampled():
         _check_rel(out[a:b].cpu().numpy(), oracle.edm(xh, i0, i1), (i0, i1))
 
 
+@pytest.mark.parametrize("d", [1, 3, 6])
+def test_edm_chunked_large_n_strip_widths(d):
+    """The chunked (store-bound) form at n = 8192 under every strip width it can take, each
+    bit-identical to the one-element-per-thread kernel, and sampled against the oracle."""
+    n = 8192
+    xh = synth.uniform_points(n, d, 5150 + d)
+    x = torch.from_numpy(xh).cuda()
+    ref, _ = _edm("LTM", "persistent", x, 16)
+    rng = np.random.default_rng(d)
+    ii = rng.integers(0, n, 100000).astype(np.uint32)
+    jj = (rng.random(100000) * (ii + 1)).astype(np.uint32)
+    pos = ii.astype(np.int64) * (ii + 1) // 2 + jj
+    _check_rel(ref[pos], oracle.edm_pairs(xh, ii, jj), ("ref", d))
+    try:
+        for w in (0, 128, 256, 512, 8192):
+            td.td_set_option("probe_strip", w)
+            for mapping, rho in (("LTM", 8), ("LTM", 32), ("BB", 16), ("REC", 16)):
+                got, st = _edm(mapping, "chunked", x, rho)
+                assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (d, w, mapping, rho)
+    finally:
+        td.td_set_option("probe_strip", 0)
+
+
 def test_edm_errors():
     x = torch.zeros(10, 3, device="cuda")
+    with pytest.raises(td.TDError):
+        td.td_edm("LTM", "chunked", torch.zeros(10, 9, device="cuda"), 16)   # chunked: d <= 8
+    with pytest.raises(td.TDError):
+        td.td_edm("LTM", "chunked", x, 64)       # chunked: rho 8, 16, 32
+    with pytest.raises(td.TDError):
+        td.td_edm("UTM", "chunked", x, 16)       # chunked: block strategies only
     with pytest.raises(td.TDError):
         td.td_edm("UTM", "grid", x, 64)          # tiled kernels serve block strategies only
     with pytest.raises(td.TDError):
