@@ -31,26 +31,17 @@ METRIC = "useful triangle pairs/s (g(lambda) probe sweep)"
 UNIT = "pairs/s"
 
 # DRAM traffic of the probe kernel (dram__bytes_read.sum + dram__bytes_write.sum), one ncu launch
-# per block side at N = 16384 (537 MB of output, above L2), in bytes per packed element.  The
-# kernel is write-only, so traffic scales with T(N); the N = 65536 figure is this times T(65536).
-# The numbers hold for the kernel sources whose digest is recorded here; once they change the
-# roofline line reports traffic as null until a new capture is taken.
+# per block side at N = 65536 (the launches the roofline line reports; two 1-pass metrics), in
+# bytes per launch.  The numbers hold for the kernel sources whose digest is recorded here; once
+# they change the roofline line reports traffic as null until a new capture is taken.
 PROBE_SOURCES = ("td_probe.cu", "td_tiles.cuh", "td_device.cuh", "td_strategies.cuh")
 PROBE_TRAFFIC = {
-    "sources_sha256": None,
-    "bytes_per_pair": {},
-    "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-               "--clock-control none -k regex:k_probe_chunked -s 3 -c 1 "
-               "python bench.py --case probe:LTM:chunked:16384:<rho> --steps 1 --warmup 3",
+    "sources_sha256": "b0b3cfd13f75c3d5e3ba78ac8c86a80f4ace5b972778389659a9e5303a2f5faf",
+    "bytes_per_launch": {8: 8541156352, 16: 8545067008, 32: 8548057600},
+    "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
+               "-k regex:k_probe_chunked -s 3 -c 1 "
+               "python bench.py --case probe:LTM:chunked:65536:<rho> --steps 1 --warmup 3",
 }
-
-
-def tri(n):
-    return n * (n + 1) // 2
-
-
-def sweep_pairs():
-    return sum(tri(N) for N in SIZES for _ in RHOS)
 
 
 def probe_sources_digest():
@@ -251,9 +242,10 @@ def run_ours(args):
     compare = {}
     for strategy in ([] if args.no_compare else STRATS):
         for sched in (("chunked", "persistent", "grid") if strategy in ("LTM", "BB", "REC") else ("persistent", "grid")):
-            cms, _, cper = timed(strategy, sched, max(3, args.steps // 2), 2, per_launch=True)
+            csteps = max(3, min(20, args.steps // 2))
+            cms, _, cper = timed(strategy, sched, csteps, 2, per_launch=True)
             compare[f"{strategy}/{sched}"] = {
-                "pairs_per_s": sweep_pairs() * max(3, args.steps // 2) / (cms / 1e3),
+                "pairs_per_s": sweep_pairs() * csteps / (cms / 1e3),
                 "ms_N65536": {str(r): statistics.median(cper[(65536, r)]) for r in RHOS},
             }
     bb = compare["BB/grid"]["ms_N65536"] if compare else {}
@@ -288,9 +280,9 @@ def run_ours(args):
     achieved = per_rho[dom]["GBps"]
     traffic, traffic_note = None, "no ncu capture recorded for these kernel sources"
     if (args.sched == "chunked" and PROBE_TRAFFIC["sources_sha256"] == probe_sources_digest()
-            and dom in PROBE_TRAFFIC["bytes_per_pair"]):
-        traffic = PROBE_TRAFFIC["bytes_per_pair"][dom] * tri(65536)
-        traffic_note = "ncu DRAM bytes at N=16384, scaled by T(65536)/T(16384) (write-only kernel)"
+            and dom in PROBE_TRAFFIC["bytes_per_launch"]):
+        traffic = PROBE_TRAFFIC["bytes_per_launch"][dom]
+        traffic_note = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one N=65536 launch at this rho"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": traffic_note, "kernel": f"g(lambda) probe, {args.sched} schedule, rho={dom}, N=65536",
                 "memset_write_GBps": memset_gbps,
@@ -306,7 +298,7 @@ def run_ours(args):
     if not args.no_e2e:
         host = torch.empty(tri(max(SIZES)), dtype=torch.int32, pin_memory=True)
         d2h = sum(4 * tri(N) for N in SIZES for _ in RHOS)
-        e2e_steps = max(2, args.steps // 4)
+        e2e_steps = max(2, min(5, args.steps // 4))
 
         def e2e_copy():
             for N in SIZES:
@@ -466,10 +458,49 @@ def run_case(args):
                       "pairs_per_s": pairs / (med / 1e3), "GBps_written": nbytes / (med / 1e3) / 1e9}), flush=True)
 
 
+def run_feature_sweep(args):
+    """The distance-map figure of Sec. IV: N = 1024 k (k = 1 .. 30), d = 1 .. 4, rho = 16, every
+    strategy under one schedule; per (d, N) the mean launch time over a replayed graph of `steps`
+    launches, and I = t_BB / t_strategy."""
+    import torch
+    from paper_1308_1419_gb300 import synth, td
+
+    sched = args.sched
+    sizes = [1024 * k for k in range(1, 31)]
+    strats = ["LTM", "BB", "RB", "REC", "UTM"] if sched != "chunked" else ["LTM", "BB", "REC"]
+    out = torch.empty(tri(max(sizes)), dtype=torch.float32, device="cuda")
+    table = {}
+    steps = max(3, min(10, args.steps))
+    for d in (1, 2, 3, 4):
+        xs = torch.from_numpy(synth.uniform_points(max(sizes), d, synth.seed_for(1) + d)).cuda()
+        per = {s: [] for s in strats}
+        for N in sizes:
+            x = xs[:N]
+            for strategy in strats:
+                # `steps` launches captured in one graph, so small launches are timed on the GPU and
+                # not by the host's call overhead
+                td.td_edm(strategy, sched, x, 16, out)
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    for _ in range(steps):
+                        td.td_edm(strategy, sched, x, 16, out)
+                graph.replay()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                graph.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                per[strategy].append(e0.elapsed_time(e1) / steps)
+        table[str(d)] = {"ms": per, "I_vs_BB": {s: [b / t for b, t in zip(per["BB"], per[s])] for s in strats}}
+    print(json.dumps({"sweep": "EDM features (Sec. IV)", "rho": 16, "schedule": sched, "N": sizes, "steps": steps,
+                      "data": "synthetic U[0,1)^d", "by_d": table}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -477,13 +508,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--sched", default="chunked", choices=["chunked", "persistent", "grid"],
                     help="schedule of the headline g(lambda) sweep")
+    ap.add_argument("--sweep", default=None, choices=["edm-features"],
+                    help="edm-features: the distance-map sweep of Sec. IV (N = 1024..30720, d = 1..4, rho 16, "
+                         "all strategies under --sched); one JSON line")
     ap.add_argument("--case", default="sweep",
                     help="sweep (default), or one kernel alone: probe:<strategy>:<sched>:<N>:<rho>, "
                          "edm:<strategy>:<sched>:<n>:<d>:<rho>, collide:<strategy>:<sched>:<n>")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.sweep == "edm-features":
+        run_feature_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.case != "sweep":
         run_case(args)
