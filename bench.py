@@ -44,6 +44,14 @@ PROBE_TRAFFIC = {
 }
 
 
+def tri(n):
+    return n * (n + 1) // 2
+
+
+def sweep_pairs():
+    return sum(tri(N) for N in SIZES for _ in RHOS)
+
+
 def probe_sources_digest():
     import hashlib
     h = hashlib.sha256()
@@ -497,6 +505,49 @@ def run_feature_sweep(args):
                       "data": "synthetic U[0,1)^d", "by_d": table}), flush=True)
 
 
+def _graph_ms(fn, steps):
+    """Mean device time of fn() over `steps` launches captured in one CUDA graph."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for _ in range(steps):
+            fn()
+    graph.replay()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_ltm_variant_sweep(args):
+    """The LTM implementation comparison of Sec. III-A: the map-only dummy kernel under BB and
+    under each evaluation of g (exact fix-up, LTM-X, LTM-N, LTM-R), N = 1024 k (k = 1 .. 30),
+    rho = 16, paper-style GRID launch; I = t_BB / t_variant.  Also each variant's first failing
+    lambda below 2^32 (the exact g has none)."""
+    import torch
+    from paper_1308_1419_gb300 import td
+
+    sizes = [1024 * k for k in range(1, 31)]
+    maps = ["BB", "LTM", "LTM-X", "LTM-N", "LTM-R"]
+    sched = args.sched if args.sched != "chunked" else "grid"
+    steps = max(3, min(10, args.steps))
+    sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ms = {m: [_graph_ms(lambda: td.td_map_dummy(m, sched, N, 16, sink), steps) for N in sizes] for m in maps}
+    first = {}
+    for m in maps[1:]:
+        r = td.td_ltm_variant_check(m, 0, 1 << 32).cpu().tolist()
+        first[m] = {"failures_below_2^32": int(r[0]), "first_failing_lambda": None if r[0] == 0 else int(r[1])}
+    print(json.dumps({"sweep": "LTM implementations (Sec. III-A), map-only dummy kernel", "rho": 16, "schedule": sched,
+                      "N": sizes, "steps": steps, "ms": ms,
+                      "I_vs_BB": {m: [b / t for b, t in zip(ms["BB"], ms[m])] for m in maps},
+                      "mean_I_vs_BB": {m: statistics.mean(b / t for b, t in zip(ms["BB"], ms[m])) for m in maps},
+                      "first_failure": first}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -508,9 +559,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
     ap.add_argument("--sched", default="chunked", choices=["chunked", "persistent", "grid"],
                     help="schedule of the headline g(lambda) sweep")
-    ap.add_argument("--sweep", default=None, choices=["edm-features"],
+    ap.add_argument("--sweep", default=None, choices=["edm-features", "ltm-variants"],
                     help="edm-features: the distance-map sweep of Sec. IV (N = 1024..30720, d = 1..4, rho 16, "
-                         "all strategies under --sched); one JSON line")
+                         "all strategies under --sched); ltm-variants: the LTM implementations of Sec. III-A "
+                         "against BB with the map-only dummy kernel; one JSON line")
     ap.add_argument("--case", default="sweep",
                     help="sweep (default), or one kernel alone: probe:<strategy>:<sched>:<N>:<rho>, "
                          "edm:<strategy>:<sched>:<n>:<d>:<rho>, collide:<strategy>:<sched>:<n>")
@@ -519,6 +571,8 @@ def main():
         args.warmup = 3
     if args.sweep == "edm-features":
         run_feature_sweep(args)
+    elif args.sweep == "ltm-variants":
+        run_ltm_variant_sweep(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.case != "sweep":

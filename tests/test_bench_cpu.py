@@ -1,0 +1,29 @@
+"""bench.py on the CPU: its helpers, and the reference arm (the oracle timed on host cores)
+end to end, printing the contract's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_helpers():
+    assert bench.tri(65536) == 65536 * 65537 // 2
+    assert bench.sweep_pairs() == 3 * sum(n * (n + 1) // 2 for n in bench.SIZES)
+    cfg = bench.headline_config("chunked")
+    assert cfg["useful_pairs_per_step"] == bench.sweep_pairs() and "chunked" in cfg["workload"]
+    assert len(bench.probe_sources_digest()) == 64
+
+
+def test_reference_arm_prints_contract_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"] == bench.headline_config("chunked")
