@@ -361,7 +361,7 @@ def run_case(args):
     from paper_1308_1419_gb300 import td
     from paper_1308_1419_gb300 import synth
     parts = args.case.split(":")
-    kind, strategy, sched = parts[:3]
+    kind, strategy, sched = (parts + ["", ""])[:3]
     if kind == "probe":
         N, rho = int(parts[3]), int(parts[4])
         out = torch.empty(tri(N), dtype=torch.int32, device="cuda")
@@ -391,6 +391,23 @@ def run_case(args):
         pairs, nbytes = n * (n - 1) // 2, 4 * td.td_collide_words(n)
         def call():
             td.td_collide(strategy, sched, ct, rt, table)
+    elif kind == "edmstrict":
+        # edmstrict:<n>:<d>: strict-lower distance map, element-level strict g
+        n, d = int(strategy), int(sched)
+        x = torch.from_numpy(synth.uniform_points(n, d, synth.seed_for(1))).cuda()
+        out = torch.empty(max(n * (n - 1) // 2, 4), dtype=torch.float32, device="cuda")
+        pairs, nbytes = n * (n - 1) // 2, 4 * (n * (n - 1) // 2)
+        def call():
+            td.td_edm_strict(x, out)
+    elif kind == "collidestrict":
+        # collidestrict:<n>: strict-lower collision bits, element-level strict g
+        n = int(strategy)
+        c, r = synth.spheres(n)
+        ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+        bits = torch.empty(max(td.td_collide_strict_words(n), 4), dtype=torch.int32, device="cuda")
+        pairs, nbytes = n * (n - 1) // 2, 4 * td.td_collide_strict_words(n)
+        def call():
+            td.td_collide_strict(ct, rt, bits)
     elif kind == "gram":
         # gram:<n>:<d>: BF16 tensor-core Gram form with FP32 direct recompute
         n, d = int(strategy), int(sched)
@@ -524,10 +541,10 @@ def _graph_ms(fn, steps):
 
 
 def run_ltm_variant_sweep(args):
-    """The LTM implementation comparison of Sec. III-A: the map-only dummy kernel under BB and
-    under each evaluation of g (exact fix-up, LTM-X, LTM-N, LTM-R), N = 1024 k (k = 1 .. 30),
-    rho = 16, paper-style GRID launch; I = t_BB / t_variant.  Also each variant's first failing
-    lambda below 2^32 (the exact g has none)."""
+    """The LTM implementation comparison of Sec. III-A: the map-only dummy kernel, and the probe
+    body, under BB and under each evaluation of g (exact fix-up, LTM-X, LTM-N, LTM-R),
+    N = 1024 k (k = 1 .. 30), rho = 16, paper-style GRID launch; I = t_BB / t_variant.  Also each
+    variant's first failing lambda below 2^32 (the exact g has none)."""
     import torch
     from paper_1308_1419_gb300 import td
 
@@ -536,7 +553,9 @@ def run_ltm_variant_sweep(args):
     sched = args.sched if args.sched != "chunked" else "grid"
     steps = max(3, min(10, args.steps))
     sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    out = torch.empty(tri(max(sizes)), dtype=torch.int32, device="cuda")
     ms = {m: [_graph_ms(lambda: td.td_map_dummy(m, sched, N, 16, sink), steps) for N in sizes] for m in maps}
+    ms_probe = {m: [_graph_ms(lambda: td.td_map_probe(m, sched, N, 16, out), steps) for N in sizes] for m in maps}
     first = {}
     for m in maps[1:]:
         r = td.td_ltm_variant_check(m, 0, 1 << 32).cpu().tolist()
@@ -545,6 +564,9 @@ def run_ltm_variant_sweep(args):
                       "N": sizes, "steps": steps, "ms": ms,
                       "I_vs_BB": {m: [b / t for b, t in zip(ms["BB"], ms[m])] for m in maps},
                       "mean_I_vs_BB": {m: statistics.mean(b / t for b, t in zip(ms["BB"], ms[m])) for m in maps},
+                      "probe_ms": ms_probe,
+                      "probe_mean_I_vs_BB": {m: statistics.mean(b / t for b, t in zip(ms_probe["BB"], ms_probe[m]))
+                                             for m in maps},
                       "first_failure": first}), flush=True)
 
 

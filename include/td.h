@@ -39,13 +39,32 @@ typedef enum {
 
 /* Mapping strategies (Sec. III-B): bounding box, upper-triangular mapping (Avril et al.),
  * rectangular box (Jung et al.), recursive partition (Ries et al.), and the paper's
- * lower-triangular mapping g(lambda) (Sec. II-A). */
+ * lower-triangular mapping g(lambda) (Sec. II-A).
+ * TD_MAP_LTM evaluates i = floor(sqrt(1/4 + 2 lambda) - 1/2) with an FP32 reciprocal-square-root
+ * estimate and an exact integer +-1 fix-up (exact for lambda < 2^40).  The three LTM_* values
+ * are the single-precision evaluations Sec. III-A times in its dummy kernel, with no fix-up;
+ * with x = 1/4 + 2 lambda rounded to FP32 and every operation rounded to nearest:
+ *   TD_MAP_LTM_X  i = trunc(sqrt(x) - 1/2)                      (LTM-X);
+ *   TD_MAP_LTM_N  y = bits^-1(0x5f3759df - (bits(x) >> 1)), three steps y = y (3/2 - ((x/2) y) y),
+ *                 i = trunc(x y - 1/2 + 1e-4)                   (LTM-N, the paper's epsilon);
+ *   TD_MAP_LTM_R  i = trunc(x rsqrtf(x) - 1/2 + 1e-4)           (LTM-R, the paper's epsilon);
+ * all with j = lambda - T(i).  They are exact only while FP32 resolves the row boundaries
+ * (td_ltm_variant_check finds where each stops); they serve td_map_probe, td_map_cover and
+ * td_map_dump under GRID or PERSISTENT, and every other call rejects them (TD_ERR_UNSUPPORTED).
+ * TD_MAP_UTM_BLOCK is the conjecture that closes the paper: the UTM formula applied to block
+ * indices lambda < T(nb) over the block triangle (rows reversed into the lower triangle, so
+ * consecutive lambda continue a block row), its square root taken as y rsqrtf(y), with UTM's
+ * integer fix-up; it is a block strategy like TD_MAP_LTM and is accepted wherever LTM is. */
 typedef enum {
     TD_MAP_BB = 0,
     TD_MAP_UTM = 1,
     TD_MAP_RB = 2,
     TD_MAP_REC = 3,
-    TD_MAP_LTM = 4
+    TD_MAP_LTM = 4,
+    TD_MAP_LTM_X = 5,
+    TD_MAP_LTM_N = 6,
+    TD_MAP_LTM_R = 7,
+    TD_MAP_UTM_BLOCK = 8
 } td_mapping;
 
 /* How the strategy's blocks are issued.
@@ -154,6 +173,24 @@ td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho
 td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                  float *out, td_launch_stats *stats, void *stream);
 
+/* td-problems without the diagonal (Eq. (theorem_nodiag)), mapped at the element level: the
+ * strict lower triangle i > j of side n has n(n-1)/2 elements, packed row-major at
+ * k = i(i-1)/2 + j, and a thread finds the (i, j) of its k with the strict g,
+ *     i = floor(sqrt(1/4 + 2k) + 1/2),  j = k - i(i-1)/2
+ * (the printed j = k - i(i+1)/2 would give j = -1 at k = 0), evaluated as an FP32 reciprocal-
+ * square-root estimate with an exact integer +-1 row fix-up.  n(n-1)/2 < 2^40.
+ *
+ * td_edm_strict: out[k] = D(i, j) in the summation order of td_edm (so out[k] equals td_edm's
+ *   out[T(i) + j] bit for bit).  x: device, float[n][d], 16-byte aligned; out: device,
+ *   float[n(n-1)/2], 16-byte aligned; d >= 1.  n < 2: no-op.
+ * td_collide_strict: bit k (word k / 32, bit k % 32, LSB first) of bits is 1 iff spheres i and
+ *   j collide, decided exactly (same predicate and input domain as td_collide); the unused
+ *   bits of the last word are 0.  centers: device int32[n][3]; radii: device int32[n];
+ *   bits: device uint32[td_collide_strict_words(n)]; all 4-byte aligned.  n < 2: no-op. */
+uint64_t td_collide_strict_words(uint32_t n); /* ceil(n(n-1)/2 / 32) */
+td_status td_edm_strict(const float *x, uint32_t n, uint32_t d, float *out, void *stream);
+td_status td_collide_strict(const int32_t *centers, const int32_t *radii, uint32_t n, uint32_t *bits, void *stream);
+
 /* Collision table (collision detection is a td-problem named in the abstract and Sec. I):
  * spheres i > j collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, decided exactly.  The table is
  * bit-packed in 32 x 32 bit-tiles over the tile triangle of side nt = ceil(n / 32): tile
@@ -260,9 +297,21 @@ td_status td_edm_batched_autotune(uint32_t nprob, const uint32_t *n, const uint3
 td_status td_map_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho,
                        uint32_t *count, void *stream);
 
+/* The dummy kernel of Sec. III-A (the timing of a mapping alone): the launch of td_map_probe,
+ * each in-domain thread computing its (i, j) through strategy m, and a store to sink[0] guarded
+ * by i + j == 2^32 - 1, which no in-domain pair meets, so the mapping cannot be optimised away
+ * and nothing is written.  (The paper stores i + j to one fixed address; on this GPU that
+ * would serialise every thread on one memory line.)  sched: GRID or PERSISTENT; every mapping,
+ * the LTM_* variants included.  sink: device, uint32[1], 4-byte aligned, left unchanged. */
+td_status td_map_dummy(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *sink,
+                       td_launch_stats *stats, void *stream);
+
 /* Dump of a mapping function for unit indices u0 .. u0+count-1 into ij (device,
  * uint32[2*count], pairs (i, j)):
  *   TD_MAP_LTM: unit = block index lambda, (i, j) = g(lambda) of Eq. (theorem); N unused.
+ *   TD_MAP_LTM_X, TD_MAP_LTM_N, TD_MAP_LTM_R: the same with that FP32 evaluation (lambda < 2^48).
+ *   TD_MAP_UTM_BLOCK: unit = block index lambda < T(N), (i, j) = its block for a block triangle of
+ *               side N (N < 2^30).
  *   TD_MAP_UTM: unit = thread index k < T(N), (i, j) = the UTM pair of Sec. III-B for the
  *               strict upper triangle of side N+1, rows reversed into the lower triangle:
  *               i = N - a, j = b - a - 1.
@@ -279,6 +328,11 @@ td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uin
  * result: device, uint64[2], must hold {0, UINT64_MAX} on entry;
  * on exit result[0] = number of failures, result[1] = smallest failing lambda. */
 td_status td_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, void *stream);
+
+/* The same count for any evaluation of g: m in {TD_MAP_LTM, TD_MAP_LTM_X, TD_MAP_LTM_N,
+ * TD_MAP_LTM_R} (td_ltm_check is m = TD_MAP_LTM).  Same result convention and range limit;
+ * other m: TD_ERR_UNSUPPORTED. */
+td_status td_ltm_variant_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t *result, void *stream);
 
 #ifdef __cplusplus
 }

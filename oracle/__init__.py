@@ -50,10 +50,15 @@ _collide = _sig("or_collide", None, _i32p, _i32p, C.c_uint32, _u32p)
 _collide_pairs = _sig("or_collide_pairs", None, _i32p, _i32p, _u32p, _u32p, C.c_uint64, _u8p)
 _collide_words = _sig("or_collide_words", C.c_uint64, C.c_uint32)
 _collide_bitpos = _sig("or_collide_bitpos", None, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32))
+_edm_strict = _sig("or_edm_strict", None, _f32p, C.c_uint32, C.c_uint32, _f64p)
+_collide_strict = _sig("or_collide_strict", None, _i32p, _i32p, C.c_uint32, _u32p)
+_fast_rsqrt = _sig("or_fast_rsqrt", C.c_float, C.c_float, C.c_int)
+_ltm_variant = _sig("or_ltm_variant", None, C.c_int, C.c_uint64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32))
+_ltm_variant_first_fail = _sig("or_ltm_variant_first_fail", C.c_uint64, C.c_int, C.c_uint64, C.c_uint64)
 
 # strategy ids used by or_cover (same numbering as the public enum, by choice, not by sharing)
-BB, UTM, RB, REC, LTM = 0, 1, 2, 3, 4
-STRATEGIES = {"BB": BB, "UTM": UTM, "RB": RB, "REC": REC, "LTM": LTM}
+BB, UTM, RB, REC, LTM, UTM_BLOCK = 0, 1, 2, 3, 4, 8
+STRATEGIES = {"BB": BB, "UTM": UTM, "RB": RB, "REC": REC, "LTM": LTM, "UTM-BLOCK": UTM_BLOCK}
 
 
 def tri(m: int) -> int:
@@ -71,6 +76,27 @@ def ltm(lam) -> np.ndarray:
     ij = np.empty(2 * lam.size, dtype=np.uint32)
     _ltm_many(lam, lam.size, ij)
     return ij.reshape(-1, 2)
+
+
+# the FP32 evaluations of g that Sec. III-A times (the two with a host definition)
+LTM_X, LTM_N = 1, 2
+
+
+def fast_rsqrt(x: float, steps: int) -> float:
+    """The bit-level inverse-square-root estimate after `steps` Newton steps, in FP32."""
+    return float(_fast_rsqrt(x, steps))
+
+
+def ltm_variant(variant: int, lam: int):
+    """(i, j) of LTM-X (variant 1) or LTM-N (variant 2) at lambda, in FP32 as defined in td_oracle.c."""
+    i, j = C.c_uint32(), C.c_uint32()
+    _ltm_variant(variant, lam, C.byref(i), C.byref(j))
+    return i.value, j.value
+
+
+def ltm_variant_first_fail(variant: int, lam0: int, lam1: int) -> int:
+    """Smallest lambda in [lam0, lam1) where the variant differs from the exact g (lam1 if none)."""
+    return int(_ltm_variant_first_fail(variant, lam0, lam1))
 
 
 def ltm_nodiag(lam) -> np.ndarray:
@@ -210,3 +236,22 @@ def collide_bitpos(i: int, j: int):
     w, b = C.c_uint64(), C.c_uint32()
     _collide_bitpos(i, j, C.byref(w), C.byref(b))
     return int(w.value), int(b.value)
+
+
+def edm_strict(x: np.ndarray) -> np.ndarray:
+    """Strict-lower distance map (no diagonal) in double: pair (i, j), i > j, at k = i(i-1)/2 + j."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n, d = x.shape
+    out = np.empty(n * (n - 1) // 2, dtype=np.float64)
+    _edm_strict(x.reshape(-1), n, d, out)
+    return out
+
+
+def collide_strict(c: np.ndarray, r: np.ndarray) -> np.ndarray:
+    """Strict-lower collision bits: bit k % 32 of word k / 32 for the pair at k = i(i-1)/2 + j."""
+    c = np.ascontiguousarray(c, dtype=np.int32).reshape(-1)
+    r = np.ascontiguousarray(r, dtype=np.int32)
+    n = r.size
+    bits = np.zeros(max((n * (n - 1) // 2 + 31) // 32, 1), dtype=np.uint32)
+    _collide_strict(c, r, n, bits)
+    return bits[: (n * (n - 1) // 2 + 31) // 32]

@@ -84,6 +84,57 @@ void or_ltm_nodiag_many(const uint64_t *lam, uint64_t count, uint32_t *ij)
     for (uint64_t q = 0; q < count; ++q) or_ltm_nodiag(lam[q], &ij[2 * q], &ij[2 * q + 1]);
 }
 
+/* ---------------------------------------------------------------- FP32 evaluations of g (Sec. III-A)
+ * Sec. III-A times ways of evaluating i = floor(sqrt(1/4 + 2 lambda) - 1/2) in single precision
+ * in its dummy kernel.  Two of them are fully specified by IEEE single-precision arithmetic and
+ * are written out here (this file is built with -ffp-contract=off, and C evaluates float
+ * expressions in float on the targets it is built for, so every operation below rounds to
+ * nearest exactly once):
+ *   variant 1 (LTM-X): x = 0.25f + 2.0f * (float)lambda;  i = trunc(sqrtf(x) - 0.5f);
+ *   variant 2 (LTM-N): the same x; y0 = the float whose bits are 0x5f3759df - (bits(x) >> 1)
+ *     (the bit-level inverse-square-root estimate analysed by Lomont), three Newton steps
+ *     y = y * (1.5f - ((0.5f * x) * y) * y), then i = trunc((x * y - 0.5f) + 1e-4f): the paper
+ *     adds epsilon = 1e-4 to the computation of i here to repair the rounding at row starts.
+ * j = lambda - T(i).  The third variant (LTM-R: x * rsqrtf(x) - 0.5 + 1e-4) depends on the
+ * device's reciprocal-square-root approximation and has no host definition. */
+
+static float bits_to_float(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
+static uint32_t float_to_bits(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+
+/* The inverse-square-root estimate refined by `steps` Newton steps (variant 2's core). */
+float or_fast_rsqrt(float x, int steps)
+{
+    const float h = 0.5f * x;
+    float y = bits_to_float(0x5f3759dfu - (float_to_bits(x) >> 1));
+    for (int k = 0; k < steps; ++k) y = y * (1.5f - (h * y) * y);
+    return y;
+}
+
+static uint32_t trunc_u32(float v) { return v <= 0.0f ? 0u : (uint32_t)v; }
+
+void or_ltm_variant(int variant, uint64_t lam, uint32_t *i, uint32_t *j)
+{
+    const float x = 0.25f + 2.0f * (float)lam;
+    uint32_t r = 0;
+    if (variant == 1) r = trunc_u32(sqrtf(x) - 0.5f);
+    if (variant == 2) r = trunc_u32((x * or_fast_rsqrt(x, 3) - 0.5f) + 1e-4f);
+    *i = r;
+    *j = (uint32_t)(lam - or_tri(r));
+}
+
+/* Smallest lambda in [lam0, lam1) whose variant (i, j) differs from the exact g(lambda), or
+ * lam1 if there is none: a plain scan. */
+uint64_t or_ltm_variant_first_fail(int variant, uint64_t lam0, uint64_t lam1)
+{
+    for (uint64_t lam = lam0; lam < lam1; ++lam) {
+        uint32_t i, j, ei, ej;
+        or_ltm_variant(variant, lam, &i, &j);
+        or_ltm(lam, &ei, &ej);
+        if (i != ei || j != ej) return lam;
+    }
+    return lam1;
+}
+
 /* ---------------------------------------------------------------- UTM, Sec. III-B */
 
 /* UTM (Avril et al.), as given in Sec. III-B: for a strict upper triangle of side n and a
@@ -169,7 +220,7 @@ int or_rec_levels(uint32_t N, uint32_t rho, uint32_t *m)
 
 /* ---------------------------------------------------------------- coverage / launch space */
 
-enum { OR_BB = 0, OR_UTM = 1, OR_RB = 2, OR_REC = 3, OR_LTM = 4 };
+enum { OR_BB = 0, OR_UTM = 1, OR_RB = 2, OR_REC = 3, OR_LTM = 4, OR_UTM_BLOCK = 8 };
 
 static void cover_one(uint32_t *count, uint32_t N, uint64_t i, uint64_t j, uint64_t *outside)
 {
@@ -206,6 +257,19 @@ int or_cover(int strategy, uint32_t N, uint32_t rho, uint32_t *count, uint64_t s
         for (uint64_t lam = 0; lam < or_tri(nb); ++lam) {
             uint32_t bi, bj;
             or_ltm(lam, &bi, &bj);
+            ++launched;
+            uint64_t before = outside;
+            for (uint64_t ty = 0; ty < rho; ++ty)
+                for (uint64_t tx = 0; tx < rho; ++tx)
+                    cover_one(count, N, (uint64_t)bi * rho + ty, (uint64_t)bj * rho + tx, &outside);
+            if (outside - before < (uint64_t)rho * rho) ++useful;
+        }
+    } else if (strategy == OR_UTM_BLOCK) {
+        /* block-level UTM (the paper's closing conjecture): block lambda < T(nb) -> the UTM
+         * pair of the block triangle of side nb, rows reversed into the lower triangle. */
+        for (uint64_t lam = 0; lam < or_tri(nb); ++lam) {
+            uint32_t bi, bj;
+            or_utm_lower((uint32_t)nb, lam, &bi, &bj);
             ++launched;
             uint64_t before = outside;
             for (uint64_t ty = 0; ty < rho; ++ty)
@@ -393,6 +457,37 @@ void or_collide(const int32_t *c, const int32_t *r, uint32_t n, uint32_t *table)
                 or_collide_bitpos(i, j, &w, &b);
                 table[w] |= (uint32_t)1 << b;
             }
+}
+
+/* ---------------------------------------------------------------- td-problems without the diagonal
+ * The strict lower triangle i > j of side n, packed row-major: pair (i, j) at k = i(i-1)/2 + j
+ * (the numbering of Eq. (theorem_nodiag), with the strict row start).  Plain double loops. */
+
+/* EDM over the strict triangle: out[k] = sqrt(sum (x_i - x_j)^2) in double. */
+void or_edm_strict(const float *x, uint32_t n, uint32_t d, double *out)
+{
+    uint64_t k = 0;
+    for (uint64_t i = 1; i < n; ++i)
+        for (uint64_t j = 0; j < i; ++j, ++k) {
+            double s = 0.0;
+            for (uint64_t f = 0; f < d; ++f) {
+                double diff = (double)x[i * d + f] - (double)x[j * d + f];
+                s += diff * diff;
+            }
+            out[k] = sqrt(s);
+        }
+}
+
+/* Collision bits over the strict triangle: bit k % 32 (LSB first) of word k / 32 is the exact
+ * predicate for the pair at k; the words must hold ceil(n(n-1)/2 / 32) entries. */
+void or_collide_strict(const int32_t *c, const int32_t *r, uint32_t n, uint32_t *bits)
+{
+    uint64_t total = (uint64_t)n * (n ? n - 1 : 0) / 2;
+    memset(bits, 0, sizeof(uint32_t) * ((total + 31) / 32));
+    uint64_t k = 0;
+    for (uint32_t i = 1; i < n; ++i)
+        for (uint32_t j = 0; j < i; ++j, ++k)
+            if (or_collides(c, r, i, j)) bits[k / 32] |= (uint32_t)1 << (k % 32);
 }
 
 void or_collide_pairs(const int32_t *c, const int32_t *r, const uint32_t *ii, const uint32_t *jj,

@@ -91,8 +91,8 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
         return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16, 32, 64 or 128 (got %u)", rho);
     if (s != TD_SCHED_GRID && s != TD_SCHED_PERSISTENT && s != TD_SCHED_CHUNKED)
         return fail(TD_ERR_INVALID_ARG, "unknown schedule %d", int(s));
-    if (s == TD_SCHED_CHUNKED && m != TD_MAP_LTM && m != TD_MAP_BB && m != TD_MAP_REC)
-        return fail(TD_ERR_UNSUPPORTED, "the chunked schedule serves the block strategies LTM, BB and REC");
+    if (s == TD_SCHED_CHUNKED && !block_strategy(m))
+        return fail(TD_ERR_UNSUPPORTED, "the chunked schedule serves the block strategies LTM, BB, REC and UTM-BLOCK");
     const bool grid = s == TD_SCHED_GRID;
     p = Plan{};
     p.nb = (N + rho - 1) / rho;
@@ -105,6 +105,10 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
         if (nb > kMaxGridY) return fail(TD_ERR_UNSUPPORTED, "BB needs ceil(N/rho) <= 65535");
         break;
     case TD_MAP_LTM:
+    case TD_MAP_LTM_X:
+    case TD_MAP_LTM_N:
+    case TD_MAP_LTM_R:
+    case TD_MAP_UTM_BLOCK:
         p.blocks = p.useful = tri(nb);
         if (grid && p.blocks > kMaxGridX) return fail(TD_ERR_UNSUPPORTED, "LTM grid launch needs T(n) < 2^31");
         break;
@@ -238,15 +242,36 @@ td_status td_map_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho
     return probe_or_cover(m, sched, N, rho, count, nullptr, stream, true);
 }
 
+td_status td_map_dummy(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, uint32_t *sink,
+                       td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    if (rho > 32) return fail(TD_ERR_INVALID_ARG, "the dummy kernel needs rho 8, 16 or 32 (got %u)", rho);
+    Plan p;
+    td_status st = plan_strategy(m, sched, N, rho, p);
+    if (st != TD_OK) return st;
+    if (N == 0) {
+        fill_stats(stats, p, 0);
+        return TD_OK;
+    }
+    if (!sink) return fail(TD_ERR_INVALID_ARG, "sink is NULL");
+    if (reinterpret_cast<uintptr_t>(sink) & 3u) return fail(TD_ERR_INVALID_ARG, "sink must be 4-byte aligned");
+    uint64_t ctas = 0;
+    st = launch_dummy(m, sched, N, rho, sink, p, static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
+}
+
 td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
                  td_launch_stats *stats, void *stream)
 {
     g_err[0] = 0;
+    if (ltm_variant(m)) return fail(TD_ERR_UNSUPPORTED, "the FP32 LTM variants serve the probe only");
     Plan p;
     td_status st = plan_strategy(m, sched, n, rho, p);
     if (st != TD_OK) return st;
-    if (rho > 32 && m != TD_MAP_LTM && m != TD_MAP_BB && m != TD_MAP_REC)
-        return fail(TD_ERR_UNSUPPORTED, "rho 64/128 (tiled EDM) supports LTM, BB and REC only");
+    if (rho > 32 && !block_strategy(m))
+        return fail(TD_ERR_UNSUPPORTED, "rho 64/128 (tiled EDM) supports LTM, BB, REC and UTM-BLOCK only");
     if (d == 0) return fail(TD_ERR_INVALID_ARG, "d must be at least 1");
     if (n == 0) {
         fill_stats(stats, p, 0);
@@ -271,13 +296,14 @@ td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, co
                      uint32_t *table, td_launch_stats *stats, void *stream)
 {
     g_err[0] = 0;
-    if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM and BB");
+    if (m != TD_MAP_LTM && m != TD_MAP_BB && m != TD_MAP_UTM_BLOCK)
+        return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM, BB and UTM-BLOCK");
     if (sched != TD_SCHED_GRID && sched != TD_SCHED_PERSISTENT)
         return fail(TD_ERR_INVALID_ARG, "td_collide takes the GRID or PERSISTENT schedule");
     const uint64_t nt = (uint64_t(n) + 31) / 32;
     Plan p;
     p.nb = static_cast<uint32_t>(nt);
-    p.blocks = m == TD_MAP_LTM ? tri(nt) : nt * nt;
+    p.blocks = m == TD_MAP_BB ? nt * nt : tri(nt);
     p.useful = tri(nt);
     p.launches = 1;
     if (n == 0) {
@@ -294,6 +320,32 @@ td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, co
     const td_status st = launch_collide(m, sched, centers, radii, n, table, static_cast<cudaStream_t>(stream), &ctas);
     fill_stats(stats, p, ctas);
     return st;
+}
+
+uint64_t td_collide_strict_words(uint32_t n) { return (uint64_t(n) * (n ? n - 1 : 0) / 2 + 31) / 32; }
+
+td_status td_edm_strict(const float *x, uint32_t n, uint32_t d, float *out, void *stream)
+{
+    g_err[0] = 0;
+    if (d == 0) return fail(TD_ERR_INVALID_ARG, "d must be at least 1");
+    if (n < 2) return TD_OK;
+    if (uint64_t(n) * (n - 1) / 2 >= (uint64_t(1) << 40))
+        return fail(TD_ERR_UNSUPPORTED, "td_edm_strict: the strict g is exact for n(n-1)/2 < 2^40");
+    if (!x || !out) return fail(TD_ERR_INVALID_ARG, "x and out must be non-NULL");
+    if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
+    return launch_edm_strict(x, n, d, out, static_cast<cudaStream_t>(stream));
+}
+
+td_status td_collide_strict(const int32_t *centers, const int32_t *radii, uint32_t n, uint32_t *bits, void *stream)
+{
+    g_err[0] = 0;
+    if (n < 2) return TD_OK;
+    if (uint64_t(n) * (n - 1) / 2 >= (uint64_t(1) << 40))
+        return fail(TD_ERR_UNSUPPORTED, "td_collide_strict: the strict g is exact for n(n-1)/2 < 2^40");
+    if (!centers || !radii || !bits) return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(centers) | reinterpret_cast<uintptr_t>(radii) | reinterpret_cast<uintptr_t>(bits)) & 3u)
+        return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be 4-byte aligned");
+    return launch_collide_strict(centers, radii, n, bits, static_cast<cudaStream_t>(stream));
 }
 
 size_t td_edm_gram_workspace(uint32_t n, uint32_t d) { return gram_workspace_bytes(n, d); }
@@ -356,13 +408,17 @@ td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_
 td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij, void *stream)
 {
     g_err[0] = 0;
-    if (m != TD_MAP_LTM && m != TD_MAP_UTM && m != TD_MAP_RB)
-        return fail(TD_ERR_UNSUPPORTED, "td_map_dump supports LTM, UTM and RB");
+    if (m != TD_MAP_LTM && m != TD_MAP_UTM && m != TD_MAP_RB && m != TD_MAP_UTM_BLOCK && !ltm_variant(m))
+        return fail(TD_ERR_UNSUPPORTED, "td_map_dump supports LTM (and its FP32 variants), UTM, UTM-BLOCK and RB");
+    if (m == TD_MAP_UTM_BLOCK && (N >= (1u << 30) || u0 + count > tri(N)))
+        return fail(TD_ERR_INVALID_ARG, "UTM-BLOCK block index must be < T(N)");
     if (count == 0) return TD_OK;
     if (!ij) return fail(TD_ERR_INVALID_ARG, "ij is NULL");
     if (!aligned16(ij)) return fail(TD_ERR_INVALID_ARG, "ij must be 16-byte aligned");
     if (m == TD_MAP_LTM && u0 + count > (uint64_t(1) << 40))
         return fail(TD_ERR_UNSUPPORTED, "LTM dump is exact for lambda < 2^40");
+    if (ltm_variant(m) && (u0 + count < u0 || u0 + count > (uint64_t(1) << 48)))
+        return fail(TD_ERR_UNSUPPORTED, "LTM variant dump covers lambda < 2^48");
     if (m == TD_MAP_UTM && (N >= (1u << 30) || u0 + count > tri(N)))
         return fail(TD_ERR_INVALID_ARG, "UTM thread index must be < T(N)");
     if (m == TD_MAP_RB) {
@@ -371,15 +427,22 @@ td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uin
     return launch_map_dump(m, N, u0, count, ij, static_cast<cudaStream_t>(stream));
 }
 
-td_status td_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, void *stream)
+td_status td_ltm_variant_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t *result, void *stream)
 {
     g_err[0] = 0;
+    if (m != TD_MAP_LTM && !ltm_variant(m))
+        return fail(TD_ERR_UNSUPPORTED, "td_ltm_variant_check takes LTM, LTM_X, LTM_N or LTM_R");
     if (!result) return fail(TD_ERR_INVALID_ARG, "result is NULL");
     if (!aligned16(result)) return fail(TD_ERR_INVALID_ARG, "result must be 16-byte aligned");
     if (lam0 + count < lam0 || lam0 + count > (uint64_t(1) << 48))
         return fail(TD_ERR_UNSUPPORTED, "td_ltm_check covers lambda < 2^48");
     if (count == 0) return TD_OK;
-    return launch_ltm_check(lam0, count, result, static_cast<cudaStream_t>(stream));
+    return launch_ltm_check(m, lam0, count, result, static_cast<cudaStream_t>(stream));
+}
+
+td_status td_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, void *stream)
+{
+    return td_ltm_variant_check(TD_MAP_LTM, lam0, count, result, stream);
 }
 
 }  // extern "C"

@@ -36,21 +36,6 @@ namespace {
 
 constexpr int kWarps = 8;
 
-__device__ __forceinline__ uint32_t absdiff(int32_t a, int32_t b)
-{
-    const int32_t d = a - b;
-    return static_cast<uint32_t>(d < 0 ? -d : d);
-}
-
-__device__ __forceinline__ bool exact_hit(const int4 &p, const int4 &q)
-{
-    const uint32_t R = static_cast<uint32_t>(p.w + q.w), R1 = R + 1;
-    const uint32_t dx = min(absdiff(p.x, q.x), R1);
-    const uint32_t dy = min(absdiff(p.y, q.y), R1);
-    const uint32_t dz = min(absdiff(p.z, q.z), R1);
-    return dx * dx + dy * dy + dz * dz <= R * R;
-}
-
 __device__ __forceinline__ bool small_coords(const int4 &p)
 {
     const int32_t lim = 1 << 23;
@@ -102,7 +87,7 @@ __global__ void __launch_bounds__(32 * kWarps)
         if (exact) {  // integer pass for the whole tile (large coordinates, or a pair in the band)
 #pragma unroll 4
             for (int r = 0; r < 32; ++r) {
-                const uint32_t b = __ballot_sync(0xffffffffu, exact_hit(rows[warp][r], pj));
+                const uint32_t b = __ballot_sync(0xffffffffu, collide_exact(rows[warp][r], pj));
                 if (lane == 0) words[warp][r] = b;
             }
         }
@@ -142,8 +127,9 @@ td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const in
     const bool P = s == TD_SCHED_PERSISTENT;
     const uint32_t nt = (n + 31) / 32;
     if (m == TD_MAP_LTM) return launch(tiles::Ltm{tri(nt)}, P, c, r, n, table, st, ctas);
+    if (m == TD_MAP_UTM_BLOCK) return launch(tiles::UtmBlk{tri(nt), nt}, P, c, r, n, table, st, ctas);
     if (m == TD_MAP_BB) return launch(tiles::Bb{uint64_t(nt) * nt, nt}, P, c, r, n, table, st, ctas);
-    return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM and BB");
+    return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM, BB and UTM-BLOCK");
 }
 
 }  // namespace td

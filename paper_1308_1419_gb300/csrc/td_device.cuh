@@ -37,34 +37,136 @@ __device__ __forceinline__ void ltm_g(uint64_t lam, uint32_t &i, uint32_t &j)
     j = static_cast<uint32_t>(lam - t);
 }
 
+// g(lambda) without the diagonal (Eq. (theorem_nodiag)): i = floor(sqrt(1/4 + 2 lambda) + 1/2),
+// with the strict triangle's own row start, j = lambda - i(i-1)/2 (the printed i(i+1)/2 gives
+// j = -1 at lambda = 0).  sqrt(1/4 + 2 lambda) + 1/2 = (sqrt(8 lambda + 1) + 1) / 2; the same
+// FP32 reciprocal-square-root estimate and exact +-1 row fix-up as ltm_g (exact for
+// lambda < 2^40).  Row i holds i elements, so 0 <= j < i.
+__device__ __forceinline__ void ltm_g_strict(uint64_t lam, uint32_t &i, uint32_t &j)
+{
+    const float y = __ull2float_rn(8ull * lam + 1ull);
+    const float s = y * rsqrtf(y);
+    uint32_t r = __float2uint_rz(fmaf(s, 0.5f, 0.5f));
+    uint64_t t = (uint64_t(r) * (r - 1)) >> 1;  // strict row start of row r (r >= 1)
+    if (t > lam) {                      // one row too far down
+        --r;
+        t -= r;
+    } else if (t + r <= lam) {          // one row too far up
+        t += r;
+        ++r;
+    }
+    i = r;
+    j = static_cast<uint32_t>(lam - t);
+}
+
+// The exact collision predicate |c_p - c_q|^2 <= (r_p + r_q)^2 in 32-bit integers, for
+// coordinates in [-2^30, 2^30) and radii in [0, 2^14]: with R = r_p + r_q <= 2^15, each |delta|
+// is clamped to R + 1 before squaring -- if all |delta| <= R nothing changes and the sum is exact
+// (< 3 (2^15)^2 < 2^32); if one exceeds R the clamped sum exceeds R^2, and so does the true one.
+__device__ __forceinline__ bool collide_exact(const int4 &p, const int4 &q)
+{
+    const uint32_t R = static_cast<uint32_t>(p.w + q.w), R1 = R + 1;
+    const int32_t ex = p.x - q.x, ey = p.y - q.y, ez = p.z - q.z;
+    const uint32_t dx = min(static_cast<uint32_t>(ex < 0 ? -ex : ex), R1);
+    const uint32_t dy = min(static_cast<uint32_t>(ey < 0 ? -ey : ey), R1);
+    const uint32_t dz = min(static_cast<uint32_t>(ez < 0 ? -ez : ez), R1);
+    return dx * dx + dy * dy + dz * dz <= R * R;
+}
+
+// g(lambda) as a functor (the mapper the LTM kernels are written against).
+struct LtmExact {
+    __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &i, uint32_t &j) const { ltm_g(lam, i, j); }
+};
+
+// The single-precision evaluations of i = floor(sqrt(1/4 + 2 lambda) - 1/2) that Sec. III-A
+// times in the dummy kernel, each written with explicitly rounded operations (no contraction)
+// so that it is one well-defined FP32 function; none carries a fix-up, so each is exact only
+// while FP32 resolves the row boundaries.  j = lambda - T(i) in 64-bit integers, truncated.
+__device__ __forceinline__ float ltm_radicand(uint64_t lam)  // x = 1/4 + 2 lambda, rounded
+{
+    return __fadd_rn(0.25f, __fmul_rn(2.0f, __ull2float_rn(lam)));
+}
+
+// LTM-X: the square root itself.
+struct LtmSqrt {
+    __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &i, uint32_t &j) const
+    {
+        i = __float2uint_rz(__fsub_rn(__fsqrt_rn(ltm_radicand(lam)), 0.5f));
+        j = static_cast<uint32_t>(lam - tri(i));
+    }
+};
+
+// LTM-N: the bit-level inverse-square-root seed 0x5f3759df - (bits(x) >> 1) (Lomont's
+// analysis of the method), three Newton steps y <- y (3/2 - (x/2) y^2), sqrt(x) = x y, and the
+// paper's epsilon 1e-4 added inside the floor.
+struct LtmNewton {
+    __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &i, uint32_t &j) const
+    {
+        const float x = ltm_radicand(lam), h = __fmul_rn(0.5f, x);
+        float y = __int_as_float(0x5f3759df - (__float_as_int(x) >> 1));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) y = __fmul_rn(y, __fsub_rn(1.5f, __fmul_rn(__fmul_rn(h, y), y)));
+        i = __float2uint_rz(__fadd_rn(__fsub_rn(__fmul_rn(x, y), 0.5f), 1e-4f));
+        j = static_cast<uint32_t>(lam - tri(i));
+    }
+};
+
+// LTM-R: x rsqrtf(x) with the paper's epsilon 1e-4 added inside the floor.
+struct LtmRsqrtEps {
+    __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &i, uint32_t &j) const
+    {
+        const float x = ltm_radicand(lam);
+        i = __float2uint_rz(__fadd_rn(__fsub_rn(__fmul_rn(x, rsqrtf(x)), 0.5f), 1e-4f));
+        j = static_cast<uint32_t>(lam - tri(i));
+    }
+};
+
 // UTM (Avril et al., Sec. III-B) for a lower triangle of side N with its diagonal.  The
 // strict upper triangle of side n = N + 1 has T(N) pairs; thread index k gives
 //   a = floor(((2n+1) - sqrt(4n^2 - 4n - 8k + 1)) / 2),  row start K(a) = (a-1)(2n-a)/2,
 //   b = (a+1) + k - K(a),
 // and (a, b) is sent to i = N - a, j = b - a - 1 = k - K(a).  The radicand is formed exactly
-// in 64-bit integers, the square root in FP32, and two integer conditionals repair a
-// one-off row (the paper's "two conditional statements").
+// in 64-bit integers, the square root in FP32, and integer row tests repair the estimate (the
+// paper's "two conditional statements" when it is off by one row).
+// RSQRT: the square root taken as y rsqrtf(y) (the reciprocal-square-root trick of Sec. III-A),
+// as the block-level UTM of the paper's conclusion uses it; the fix-up keeps both exact.
+template <bool RSQRT = false>
 __device__ __forceinline__ void utm_map(uint64_t k, uint32_t N, uint32_t &i, uint32_t &j)
 {
     const uint64_t n = static_cast<uint64_t>(N) + 1;
-    const uint64_t D = 4 * n * n - 4 * n - 8 * k + 1;
-    const float af = (__ull2float_rn(2 * n + 1) - sqrtf(__ull2float_rn(D))) * 0.5f;
+    const uint64_t D = 4 * n * n - 4 * n - 8 * k + 1;  // >= 9 for k < T(N)
+    const float y = __ull2float_rn(D);
+    const float af = (__ull2float_rn(2 * n + 1) - (RSQRT ? y * rsqrtf(y) : sqrtf(y))) * 0.5f;
     uint64_t a = __float2ull_rz(af);
     a = a < 1 ? 1 : (a > n - 1 ? n - 1 : a);
+    // walk to the row with K(a) <= k < K(a + 1); K(1) = 0 <= k and K(n) = T(N) > k bound it.
+    // The estimate is within one row for N below about 2^22 (one step, as the paper's two
+    // conditionals); the FP32 error grows as N 2^-24, and the walk keeps larger N exact.
     uint64_t K = ((a - 1) * (2 * n - a)) >> 1;
-    if (K > k) {
+    while (K > k) {
         --a;
         K = ((a - 1) * (2 * n - a)) >> 1;
-    } else {
+    }
+    for (;;) {
         const uint64_t K1 = (a * (2 * n - a - 1)) >> 1;
-        if (K1 <= k) {
-            ++a;
-            K = K1;
-        }
+        if (K1 > k) break;
+        ++a;
+        K = K1;
     }
     i = static_cast<uint32_t>(n - 1 - a);
     j = static_cast<uint32_t>(k - K);
 }
+
+// Block-level UTM (the conjecture that closes the paper): the UTM formula applied to block indices
+// lambda < T(nb) over the block triangle of side nb instead of to thread indices, with the
+// reciprocal-square-root trick; blocks come row by row from the last block row up.
+struct UtmBlock {
+    uint32_t nb;
+    __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &bi, uint32_t &bj) const
+    {
+        utm_map<true>(lam, nb, bi, bj);
+    }
+};
 
 // RB (Jung et al., Sec. III-B): the part of the triangle right of the middle column is
 // rotated onto the space above the diagonal, giving a thread rectangle of T(N) threads.

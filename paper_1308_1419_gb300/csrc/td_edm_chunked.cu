@@ -154,6 +154,8 @@ td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float
 {
     switch (m) {
     case TD_MAP_LTM: return launch_tiles<tiles::Ltm, RHO, D>(tiles::Ltm{tri(p.nb)}, x, n, d, out, st, ctas);
+    case TD_MAP_UTM_BLOCK:
+        return launch_tiles<tiles::UtmBlk, RHO, D>(tiles::UtmBlk{tri(p.nb), p.nb}, x, n, d, out, st, ctas);
     case TD_MAP_BB:
         return launch_tiles<tiles::Bb, RHO, D>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, x, n, d, out, st, ctas);
     case TD_MAP_REC: {

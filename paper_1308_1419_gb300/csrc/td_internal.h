@@ -34,9 +34,12 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
                        bool cover, const Plan &p, cudaStream_t st, uint64_t *ctas);
 // Strip width (elements of one packed row) of the chunked schedule: the widest power of two in
-// [256, wauto] leaving at least four strips per resident warp, or the TD_OPT_PROBE_STRIP value
-// (capped at wlimit); never below rho.
+// [256, wauto] leaving at least four strips per resident warp; below 256 (down to rho, one block
+// per strip) while there are fewer strips than resident warps; or the TD_OPT_PROBE_STRIP value
+// (capped at wlimit).  Never below rho.
 uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit);
+td_status launch_edm_strict(const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st);
+td_status launch_collide_strict(const int32_t *c, const int32_t *r, uint32_t n, uint32_t *bits, cudaStream_t st);
 td_status launch_edm_chunked(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
                              const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_pair(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
@@ -53,6 +56,15 @@ td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cu
 int option(td_option opt);
 td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,
                           cudaStream_t st);
-td_status launch_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st);
+td_status launch_dummy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *sink, const Plan &p,
+                       cudaStream_t st, uint64_t *ctas);
+td_status launch_ltm_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st);
+// The FP32 evaluations of g timed in Sec. III-A (probe, cover and dump only).
+inline bool ltm_variant(td_mapping m) { return m == TD_MAP_LTM_X || m == TD_MAP_LTM_N || m == TD_MAP_LTM_R; }
+// Strategies whose unit is a whole square block and that have a tile source (td_tiles.cuh).
+inline bool block_strategy(td_mapping m)
+{
+    return m == TD_MAP_LTM || m == TD_MAP_BB || m == TD_MAP_REC || m == TD_MAP_UTM_BLOCK;
+}
 
 }  // namespace td

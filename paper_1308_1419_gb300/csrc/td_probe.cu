@@ -17,6 +17,18 @@ struct ProbeBody {
     }
 };
 
+// The dummy kernel of Sec. III-A / IV test 1 as a map-only body: the thread's (i, j) feeds a store
+// that no in-domain pair reaches (i + j <= 2N - 2 < 2^32 - 1), so the mapping cannot be
+// optimised away, yet nothing is written (the paper's store of i + j to one fixed address
+// would serialise every thread of the launch on one L2 line here).
+struct DummyBody {
+    uint32_t *sink;
+    __device__ __forceinline__ void operator()(uint32_t i, uint32_t j) const
+    {
+        if (i + j == 0xFFFFFFFFu) *sink = i;
+    }
+};
+
 struct CoverBody {
     uint32_t *count;
     __device__ __forceinline__ void operator()(uint32_t i, uint32_t j) const
@@ -129,6 +141,8 @@ td_status launch_chunked_rho(td_mapping m, uint32_t N, uint32_t *out, const Plan
 {
     switch (m) {
     case TD_MAP_LTM: return launch_chunked_tiles<tiles::Ltm, RHO>(tiles::Ltm{tri(p.nb)}, N, out, st, ctas);
+    case TD_MAP_UTM_BLOCK:
+        return launch_chunked_tiles<tiles::UtmBlk, RHO>(tiles::UtmBlk{tri(p.nb), p.nb}, N, out, st, ctas);
     case TD_MAP_BB:
         return launch_chunked_tiles<tiles::Bb, RHO>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, N, out, st, ctas);
     case TD_MAP_REC: {
@@ -156,6 +170,14 @@ __global__ void k_map_dump(int m, uint32_t N, uint32_t W, uint64_t u0, uint64_t 
         uint32_t i, j;
         if (m == TD_MAP_LTM) {
             ltm_g(u, i, j);
+        } else if (m == TD_MAP_LTM_X) {
+            LtmSqrt{}(u, i, j);
+        } else if (m == TD_MAP_LTM_N) {
+            LtmNewton{}(u, i, j);
+        } else if (m == TD_MAP_LTM_R) {
+            LtmRsqrtEps{}(u, i, j);
+        } else if (m == TD_MAP_UTM_BLOCK) {
+            UtmBlock{N}(u, i, j);
         } else if (m == TD_MAP_UTM) {
             utm_map(u, N, i, j);
         } else {
@@ -167,6 +189,9 @@ __global__ void k_map_dump(int m, uint32_t N, uint32_t W, uint64_t u0, uint64_t 
     }
 }
 
+// Counts the lambda whose (i, j) from Map breaks T(i) <= lambda <= T(i) + i, j = lambda - T(i)
+// (exact 64-bit arithmetic), and the smallest such lambda.
+template <class Map>
 __global__ void k_ltm_check(uint64_t lam0, uint64_t count, unsigned long long *res)
 {
     unsigned long long bad = 0, first = ~0ull;
@@ -174,7 +199,7 @@ __global__ void k_ltm_check(uint64_t lam0, uint64_t count, unsigned long long *r
     for (uint64_t q = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < count; q += stride) {
         const uint64_t lam = lam0 + q;
         uint32_t i, j;
-        ltm_g(lam, i, j);
+        Map{}(lam, i, j);
         const uint64_t t = tri(i);
         const bool ok = t <= lam && lam - t <= i && uint64_t(j) == lam - t;
         if (!ok) {
@@ -193,6 +218,33 @@ __global__ void k_ltm_check(uint64_t lam0, uint64_t count, unsigned long long *r
     }
 }
 
+// The Sec. III-A evaluations of g in the paper-style LTM kernel (one CTA or grid-stride step per
+// block, one element per thread).
+template <class Map, class Body>
+td_status launch_variant_map(bool P, uint32_t N, uint32_t rho, Body body, const Plan &p, cudaStream_t st,
+                             uint64_t *ctas)
+{
+    switch (rho) {
+    case 8: strat::launch_ltm<8, Body, Map>(P, N, body, p, st, ctas); break;
+    case 16: strat::launch_ltm<16, Body, Map>(P, N, body, p, st, ctas); break;
+    case 32: strat::launch_ltm<32, Body, Map>(P, N, body, p, st, ctas); break;
+    default: return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32 (got %u)", rho);
+    }
+    return launch_status("td probe/cover kernel (LTM variant)");
+}
+
+template <class Body>
+td_status launch_variant(td_mapping m, bool P, uint32_t N, uint32_t rho, Body body, const Plan &p, cudaStream_t st,
+                         uint64_t *ctas)
+{
+    switch (m) {
+    case TD_MAP_LTM_X: return launch_variant_map<LtmSqrt>(P, N, rho, body, p, st, ctas);
+    case TD_MAP_LTM_N: return launch_variant_map<LtmNewton>(P, N, rho, body, p, st, ctas);
+    case TD_MAP_LTM_R: return launch_variant_map<LtmRsqrtEps>(P, N, rho, body, p, st, ctas);
+    default: return fail(TD_ERR_INVALID_ARG, "not an LTM variant (%d)", int(m));
+    }
+}
+
 }  // namespace
 
 uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit)
@@ -203,8 +255,19 @@ uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_war
         w = uint32_t(forced) < wlimit ? uint32_t(forced) : wlimit;
     } else {
         while (w < wauto && units * rho / (2 * w) >= 4 * resident_warps) w *= 2;
+        // small launch: rather one block per strip than fewer strips than resident warps (a
+        // warp walking a long strip alone on its SM exposes every instruction's latency)
+        while (w > rho && units * rho / w < resident_warps) w /= 2;
     }
     return w < rho ? rho : w;
+}
+
+td_status launch_dummy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *sink, const Plan &p,
+                       cudaStream_t st, uint64_t *ctas)
+{
+    if (s == TD_SCHED_CHUNKED) return fail(TD_ERR_UNSUPPORTED, "the dummy kernel uses the GRID or PERSISTENT schedule");
+    if (ltm_variant(m)) return launch_variant(m, s == TD_SCHED_PERSISTENT, N, rho, DummyBody{sink}, p, st, ctas);
+    return strat::launch_body(m, s, N, rho, DummyBody{sink}, p, st, ctas);
 }
 
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out, bool cover,
@@ -218,6 +281,11 @@ td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, ui
         case 32: return launch_chunked_rho<32>(m, N, out, p, st, ctas);
         default: return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32");
         }
+    }
+    if (ltm_variant(m)) {
+        const bool P = s == TD_SCHED_PERSISTENT;
+        if (cover) return launch_variant(m, P, N, rho, CoverBody{out}, p, st, ctas);
+        return launch_variant(m, P, N, rho, ProbeBody{out, N}, p, st, ctas);
     }
     if (cover) return strat::launch_body(m, s, N, rho, CoverBody{out}, p, st, ctas);
     return strat::launch_body(m, s, N, rho, ProbeBody{out, N}, p, st, ctas);
@@ -233,11 +301,18 @@ td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count,
     return launch_status("td_map_dump kernel");
 }
 
-td_status launch_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st)
+td_status launch_ltm_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st)
 {
     const uint64_t blocks = (count + 255) / 256;
     const uint32_t g = static_cast<uint32_t>(blocks < uint64_t(sm_count()) * 16 ? blocks : uint64_t(sm_count()) * 16);
-    k_ltm_check<<<g, 256, 0, st>>>(lam0, count, reinterpret_cast<unsigned long long *>(result));
+    auto *res = reinterpret_cast<unsigned long long *>(result);
+    switch (m) {
+    case TD_MAP_LTM: k_ltm_check<LtmExact><<<g, 256, 0, st>>>(lam0, count, res); break;
+    case TD_MAP_LTM_X: k_ltm_check<LtmSqrt><<<g, 256, 0, st>>>(lam0, count, res); break;
+    case TD_MAP_LTM_N: k_ltm_check<LtmNewton><<<g, 256, 0, st>>>(lam0, count, res); break;
+    case TD_MAP_LTM_R: k_ltm_check<LtmRsqrtEps><<<g, 256, 0, st>>>(lam0, count, res); break;
+    default: return fail(TD_ERR_UNSUPPORTED, "td_ltm_variant_check takes LTM, LTM_X, LTM_N or LTM_R");
+    }
     return launch_status("td_ltm_check kernel");
 }
 

@@ -21,14 +21,15 @@ namespace strat {
 // ---------------------------------------------------------------- LTM, Sec. II-A
 // Block lambda in [0, T(n)) -> (block row, block column) = g(lambda); diagonal blocks filter
 // their upper threads, edge blocks their threads beyond N.
-template <int RHO, bool P, class Body>
-__global__ void __launch_bounds__(RHO * RHO) k_ltm(uint32_t N, uint64_t units, Body body)
+// Map: the evaluation of g -- LtmExact, or one of the Sec. III-A variants (td_device.cuh).
+template <int RHO, bool P, class Body, class Map = LtmExact>
+__global__ void __launch_bounds__(RHO * RHO) k_ltm(uint32_t N, uint64_t units, Body body, Map map)
 {
     const uint32_t ty = threadIdx.x / RHO, tx = threadIdx.x % RHO;
     const uint64_t stride = P ? gridDim.x : units;
     for (uint64_t lam = blockIdx.x; lam < units; lam += stride) {
         uint32_t bi, bj;
-        ltm_g(lam, bi, bj);
+        map(lam, bi, bj);
         const uint32_t i = bi * RHO + ty, j = bj * RHO + tx;
         if (j <= i && i < N) body(i, j);
     }
@@ -150,25 +151,35 @@ uint64_t grid_for(K kernel, bool P, int threads, uint64_t units)
     return P ? persistent_ctas(reinterpret_cast<const void *>(kernel), threads, 0, units) : units;
 }
 
+// Blocks lambda < T(nb) mapped by `map` (g(lambda), one of its FP32 variants, or block-level UTM).
+template <int RHO, class Body, class Map>
+void launch_ltm(bool P, uint32_t N, Body body, const Plan &p, cudaStream_t st, uint64_t *ctas, Map map = Map{})
+{
+    constexpr int threads = RHO * RHO;
+    const uint64_t units = tri(p.nb);
+    if (P) {
+        auto k = k_ltm<RHO, true, Body, Map>;
+        const uint64_t g = grid_for(k, true, threads, units);
+        k<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, units, body, map);
+        *ctas += g;
+    } else {
+        k_ltm<RHO, false, Body, Map><<<dim3(static_cast<uint32_t>(units)), threads, 0, st>>>(N, units, body, map);
+        *ctas += units;
+    }
+}
+
 template <int RHO, class Body>
 td_status launch_rho(td_mapping m, bool P, uint32_t N, Body body, const Plan &p, cudaStream_t st,
                      uint64_t *ctas)
 {
     constexpr int threads = RHO * RHO;
     switch (m) {
-    case TD_MAP_LTM: {
-        const uint64_t units = tri(p.nb);
-        if (P) {
-            auto k = k_ltm<RHO, true, Body>;
-            const uint64_t g = grid_for(k, true, threads, units);
-            k<<<dim3(static_cast<uint32_t>(g)), threads, 0, st>>>(N, units, body);
-            *ctas += g;
-        } else {
-            k_ltm<RHO, false, Body><<<dim3(static_cast<uint32_t>(units)), threads, 0, st>>>(N, units, body);
-            *ctas += units;
-        }
+    case TD_MAP_LTM:
+        launch_ltm<RHO, Body, LtmExact>(P, N, body, p, st, ctas);
         break;
-    }
+    case TD_MAP_UTM_BLOCK:
+        launch_ltm<RHO, Body, UtmBlock>(P, N, body, p, st, ctas, UtmBlock{p.nb});
+        break;
     case TD_MAP_BB: {
         if (P) {
             auto k = k_bb_persist<RHO, Body>;

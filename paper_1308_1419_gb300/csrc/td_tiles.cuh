@@ -27,6 +27,22 @@ struct Ltm {
     }
 };
 
+// Block-level UTM: unit = block index lambda < T(nb), mapped by the UTM formula with the
+// reciprocal-square-root trick; consecutive units continue a block row from its first block.
+struct UtmBlk {
+    uint64_t units;
+    uint32_t nb;
+    __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
+    {
+        UtmBlock{nb}(u, bi, bj);
+        return true;
+    }
+    __device__ __forceinline__ uint32_t run(uint64_t, bool, uint32_t bi, uint32_t bj, uint32_t cap) const
+    {
+        return min(cap, bi - bj + 1);  // the rest of block row bi
+    }
+};
+
 // BB: unit = by * nb + bx over the n x n bounding box; blocks above the diagonal are skipped.
 struct Bb {
     uint64_t units;

@@ -17,7 +17,7 @@ if not os.path.exists(_PATH):
                       "needs nvcc with sm_103a support)")
 lib = C.CDLL(_PATH)
 
-MAPPINGS = {"BB": 0, "UTM": 1, "RB": 2, "REC": 3, "LTM": 4}
+MAPPINGS = {"BB": 0, "UTM": 1, "RB": 2, "REC": 3, "LTM": 4, "LTM-X": 5, "LTM-N": 6, "LTM-R": 7, "UTM-BLOCK": 8}
 SCHEDULES = {"grid": 0, "persistent": 1, "chunked": 2}
 STATUS = {0: "TD_OK", 1: "TD_ERR_INVALID_ARG", 2: "TD_ERR_UNSUPPORTED", 3: "TD_ERR_CUDA", 4: "TD_ERR_TIMEOUT"}
 
@@ -77,6 +77,11 @@ _c_partition = _sig("td_partition", _int, _u32, _u32, _u32, _u32, C.POINTER(C.c_
 _c_map_cover = _sig("td_map_cover", _int, _int, _int, _u32, _u32, _vp, _vp)
 _c_map_dump = _sig("td_map_dump", _int, _int, _u32, _u64, _u64, _vp, _vp)
 _c_ltm_check = _sig("td_ltm_check", _int, _u64, _u64, _vp, _vp)
+_c_ltm_variant_check = _sig("td_ltm_variant_check", _int, _int, _u64, _u64, _vp, _vp)
+_c_map_dummy = _sig("td_map_dummy", _int, _int, _int, _u32, _u32, _vp, _vp, _vp)
+_c_collide_strict_words = _sig("td_collide_strict_words", _u64, _u32)
+_c_edm_strict = _sig("td_edm_strict", _int, _vp, _u32, _u32, _vp, _vp)
+_c_collide_strict = _sig("td_collide_strict", _int, _vp, _vp, _u32, _vp, _vp)
 
 
 def _check(status):
@@ -162,6 +167,47 @@ def td_map_probe(mapping, schedule, N: int, rho: int, out: torch.Tensor = None, 
     st = td_launch_stats()
     _check(_c_map_probe(_mapping(mapping), _schedule(schedule), N, rho, ptr, C.byref(st), _stream(stream)))
     return out, st.as_dict()
+
+
+def td_map_dummy(mapping, schedule, N: int, rho: int, sink: torch.Tensor = None, stream=None):
+    """The map-only dummy kernel (Sec. III-A): launch stats; sink (int32[1]) is left unchanged."""
+    if sink is None:
+        sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    ptr = _dev(sink, torch.int32, 1, "sink")
+    st = td_launch_stats()
+    _check(_c_map_dummy(_mapping(mapping), _schedule(schedule), N, rho, ptr, C.byref(st), _stream(stream)))
+    return sink, st.as_dict()
+
+
+def td_collide_strict_words(n: int) -> int:
+    return int(_c_collide_strict_words(n))
+
+
+def td_edm_strict(x: torch.Tensor, out: torch.Tensor = None, stream=None):
+    """Packed strict-lower distance map (no diagonal): float32[n(n-1)/2], k = i(i-1)/2 + j."""
+    if x.dim() != 2:
+        raise ValueError("x must be a 2-D (n, d) tensor")
+    n, d = x.shape
+    xp = _dev(x, torch.float32, n * d, "x")
+    total = n * (n - 1) // 2
+    if out is None:
+        out = torch.empty(max(total, 4), dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, total, "out")
+    _check(_c_edm_strict(xp, n, d, op, _stream(stream)))
+    return out
+
+
+def td_collide_strict(centers: torch.Tensor, radii: torch.Tensor, bits: torch.Tensor = None, stream=None):
+    """Strict-lower collision bits (int32 tensor of uint32 words): bit k for pair k = i(i-1)/2 + j."""
+    n = radii.numel()
+    cp = _dev(centers, torch.int32, 3 * n, "centers")
+    rp = _dev(radii, torch.int32, n, "radii")
+    words = td_collide_strict_words(n)
+    if bits is None:
+        bits = torch.empty(max(words, 4), dtype=torch.int32, device=radii.device)
+    bp = _dev(bits, torch.int32, words, "bits")
+    _check(_c_collide_strict(cp, rp, n, bp, _stream(stream)))
+    return bits
 
 
 def td_edm(mapping, schedule, x: torch.Tensor, rho: int, out: torch.Tensor = None, stream=None):
@@ -332,4 +378,13 @@ def td_ltm_check(lam0: int, count: int, result: torch.Tensor = None, stream=None
         result = torch.tensor([0, -1], dtype=torch.int64, device="cuda")
     ptr = _dev(result, torch.int64, 2, "result")
     _check(_c_ltm_check(lam0, count, ptr, _stream(stream)))
+    return result
+
+
+def td_ltm_variant_check(mapping, lam0: int, count: int, result: torch.Tensor = None, stream=None):
+    """(failures, first failing lambda or -1) of an evaluation of g over [lam0, lam0 + count)."""
+    if result is None:
+        result = torch.tensor([0, -1], dtype=torch.int64, device="cuda")
+    ptr = _dev(result, torch.int64, 2, "result")
+    _check(_c_ltm_variant_check(_mapping(mapping), lam0, count, ptr, _stream(stream)))
     return result

@@ -37,7 +37,7 @@ def test_sizes():
         assert td.td_collide_words(n) == oracle.collide_words(n)
 
 
-@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB", "REC"])
+@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB", "REC", "UTM-BLOCK"])
 @pytest.mark.parametrize("N,rho", [(1, 8), (100, 8), (1024, 16), (1000, 8), (768, 16), (2048, 32)])
 def test_plan_matches_oracle_launch_space(strategy, N, rho):
     if strategy == "REC" and N % rho:

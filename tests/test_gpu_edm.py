@@ -17,7 +17,7 @@ if not torch.cuda.is_available():
 from paper_1308_1419_gb300 import td  # noqa: E402
 
 RTOL = 2e-6        # stated agreement for the FP32 distance map
-STRATS = ["BB", "UTM", "RB", "REC", "LTM"]
+STRATS = ["BB", "UTM", "RB", "REC", "LTM", "UTM-BLOCK"]
 
 
 def _check_rel(got, want, ctx):
@@ -33,7 +33,7 @@ def _edm(mapping, sched, x, rho):
 
 
 def _cases(mapping, rho, n):
-    if rho > 32 and mapping not in ("LTM", "BB", "REC"):
+    if rho > 32 and mapping not in ("LTM", "BB", "REC", "UTM-BLOCK"):
         return False
     if mapping == "REC" and n % rho:
         return False
@@ -68,7 +68,7 @@ def test_edm_ragged_all_kernels(d):
             for mapping in STRATS:
                 if not _cases(mapping, rho, n):
                     continue
-                chunked = rho <= 32 and d <= 8 and mapping in ("LTM", "BB", "REC")
+                chunked = rho <= 32 and d <= 8 and mapping in ("LTM", "BB", "REC", "UTM-BLOCK")
                 for sched in ("grid", "persistent") + (("chunked",) if chunked else ()):
                     got, _ = _edm(mapping, sched, x, rho)
                     _check_rel(got, want, (n, d, rho, mapping, sched))

@@ -17,7 +17,7 @@ if not torch.cuda.is_available():
 
 from paper_1308_1419_gb300 import td  # noqa: E402
 
-STRATS = ["BB", "UTM", "RB", "REC", "LTM"]
+STRATS = ["BB", "UTM", "RB", "REC", "LTM", "UTM-BLOCK"]
 SCHEDS = ["grid", "persistent"]
 SENTINEL = -559038737  # 0xDEADBEEF
 
@@ -32,7 +32,7 @@ def _u32(t):
 
 
 def _supported(strategy, N, rho, sched="grid"):
-    if sched == "chunked" and strategy not in ("LTM", "BB", "REC"):
+    if sched == "chunked" and strategy not in ("LTM", "BB", "REC", "UTM-BLOCK"):
         return False
     return not (strategy == "REC" and (N == 0 or N % rho))
 
@@ -169,3 +169,31 @@ def test_rb_dump_matches_oracle():
         got = td.td_map_dump("RB", N, 0, cnt)[: 2 * cnt].cpu().numpy().view(np.uint32).reshape(-1, 2)
         for u in range(0, cnt, max(1, cnt // 5000)):
             assert tuple(got[u]) == oracle.rb_map(N, u % W, u // W), (N, u)
+
+
+def test_utm_block_dump_matches_oracle_formula():
+    """Block-level UTM (rsqrt estimate + integer fix-up) equals the exact UTM formula of the
+    oracle at every block index of several block triangles, and on random indices of large ones."""
+    rng = np.random.default_rng(5)
+    for nb in [1, 2, 3, 17, 64, 1000, 1920, 8192]:
+        total = nb * (nb + 1) // 2
+        cnt = min(total, 1 << 21)
+        got = td.td_map_dump("UTM-BLOCK", nb, 0, cnt)[: 2 * cnt].cpu().numpy().view(np.uint32).reshape(-1, 2)
+        assert np.array_equal(got, oracle.utm_lower(nb, np.arange(cnt, dtype=np.uint64))), nb
+    for nb in [65535, 1 << 20, (1 << 30) - 1]:
+        total = nb * (nb + 1) // 2
+        for u0 in [0, total // 3, total - 4096] + [int(v) for v in rng.integers(0, total - 4096, 4)]:
+            got = td.td_map_dump("UTM-BLOCK", nb, u0, 4096)[: 8192].cpu().numpy().view(np.uint32).reshape(-1, 2)
+            want = oracle.utm_lower(nb, np.arange(u0, u0 + 4096, dtype=np.uint64))
+            assert np.array_equal(got, want), (nb, u0)
+
+
+def test_utm_thread_dump_large_n():
+    """Thread-level UTM near its limit N < 2^30, where the FP32 estimate can be rows off."""
+    rng = np.random.default_rng(9)
+    for N in [1 << 22, (1 << 26) + 3, (1 << 30) - 1]:
+        total = N * (N + 1) // 2
+        for u0 in [0, total - 4096] + [int(v) for v in rng.integers(0, total - 4096, 4)]:
+            got = td.td_map_dump("UTM", N, u0, 4096)[: 8192].cpu().numpy().view(np.uint32).reshape(-1, 2)
+            want = oracle.utm_lower(N, np.arange(u0, u0 + 4096, dtype=np.uint64))
+            assert np.array_equal(got, want), (N, u0)

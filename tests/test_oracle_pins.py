@@ -84,6 +84,53 @@ def test_ltm_row_boundaries_up_to_2_40():
     assert [tuple(v) for v in ij.tolist()] == want
 
 
+# ------------------------------------------------------------------ FP32 evaluations of g (Sec. III-A)
+
+def test_fast_rsqrt_error_matches_lomont():
+    """The bit-level estimate with 0x5f3759df has a maximum relative error of about 3.44%, and
+    0.175% after one Newton step (Lomont's analysis of the constant); each further step about
+    squares the error.  The relative error repeats with period 4 in x, and the estimate of 4x is
+    exactly half the estimate of x (the exponent field moves by one)."""
+    xs = [float(np.float32(x)) for x in np.linspace(1.0, 4.0, 20001)]
+    errs = [max(abs(oracle.fast_rsqrt(x, s) * math.sqrt(x) - 1.0) for x in xs) for s in range(4)]
+    assert 0.0340 < errs[0] < 0.0345
+    assert 0.00174 < errs[1] < 0.001753
+    assert errs[2] < 5e-6 and errs[3] < 3e-7
+    for x in (1.0, 1.3, 2.7, 3.9, 1e3, 7e5):
+        xf = float(np.float32(x))
+        assert oracle.fast_rsqrt(4.0 * xf, 0) == oracle.fast_rsqrt(xf, 0) / 2.0
+
+
+def _row(lam):
+    return (math.isqrt(8 * lam + 1) - 1) // 2   # exact row of lambda, independent of the oracle
+
+
+def test_ltm_x_exact_while_fp32_resolves_row_starts():
+    """LTM-X: below T(2048), x = 2 lambda + 1/4 is exact in FP32 (two fraction bits, below 2^22)
+    and sqrtf is correctly rounded, so a row start T(r), where sqrt(x) = r + 1/2 exactly, lands
+    on the right row: no failure there.  The first failure lies on a row boundary and is genuine."""
+    f = oracle.ltm_variant_first_fail(oracle.LTM_X, 0, 1 << 26)
+    assert oracle.tri(2048) <= f < 1 << 26
+    r = _row(f)
+    assert f in (oracle.tri(r), oracle.tri(r + 1) - 1)
+    assert oracle.ltm_variant(oracle.LTM_X, f)[0] != r
+    for lam in (0, 1, 2, 3, 5, 6, oracle.tri(2047), oracle.tri(2048) - 1, f - 1):
+        assert oracle.ltm_variant(oracle.LTM_X, lam) == (_row(lam), lam - oracle.tri(_row(lam)))
+
+
+def test_ltm_n_with_epsilon():
+    """LTM-N: after three Newton steps y is within 3e-7 of 1/sqrt(x), so at a row start the
+    computed x y - 1/2 is at most (r + 1/2) 3e-7 below r, which the epsilon 1e-4 covers while
+    r < 300.  The first failure lies on a row boundary and is genuine."""
+    f = oracle.ltm_variant_first_fail(oracle.LTM_N, 0, 1 << 26)
+    assert oracle.tri(300) <= f < 1 << 26
+    r = _row(f)
+    assert f in (oracle.tri(r), oracle.tri(r + 1) - 1)
+    assert oracle.ltm_variant(oracle.LTM_N, f)[0] != r
+    for lam in (0, 1, 2, 3, 4, 5, oracle.tri(299), f - 1):
+        assert oracle.ltm_variant(oracle.LTM_N, lam) == (_row(lam), lam - oracle.tri(_row(lam)))
+
+
 def test_ltm_nodiag_is_inverse_of_strict_walk():
     # strict walk: row i holds i blocks (row 0 is empty)
     i, j = _enumerate_lower(3000, diag=False)
@@ -125,7 +172,7 @@ def test_utm_lower_covers_triangle():
 
 # ------------------------------------------------------------------ all strategies: bijection
 
-@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB"])
+@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB", "UTM-BLOCK"])
 def test_strategy_bijection_small_all_N(strategy):
     for rho in (8, 16):
         for N in range(1, 97):
@@ -134,7 +181,7 @@ def test_strategy_bijection_small_all_N(strategy):
             assert st["hits"] == N * (N + 1) // 2
 
 
-@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB", "REC"])
+@pytest.mark.parametrize("strategy", ["BB", "LTM", "UTM", "RB", "REC", "UTM-BLOCK"])
 @pytest.mark.parametrize("N,rho", [(1024, 8), (1024, 16), (1024, 32), (1000, 8), (2048, 32), (768, 16), (1536, 8)])
 def test_strategy_bijection_sizes(strategy, N, rho):
     if strategy == "REC" and N % rho:
@@ -385,3 +432,32 @@ def test_synth_streams():
     ns, ds, x = synth.batched_problems()
     assert ns.size == 512 and ns.min() >= 64 and ns.max() < 8192
     assert set(ds.tolist()) <= {3, 16, 64} and x.size == int((ns.astype(np.int64) * ds).sum())
+
+
+# ------------------------------------------------------------------ td-problems without the diagonal
+
+@pytest.mark.parametrize("n,d", [(2, 1), (3, 3), (40, 2), (129, 4), (300, 7)])
+def test_edm_strict_matches_scipy_pdist(n, d):
+    """pdist lists the pairs j < i in its own order (row j of the upper triangle); the strict
+    packed index k = i(i-1)/2 + j of the same pair picks the same distance."""
+    from scipy.spatial.distance import pdist
+    x = synth.uniform_points(n, d, 77 + n)
+    got = oracle.edm_strict(x)
+    ref = pdist(x.astype(np.float64))
+    i, j = np.tril_indices(n, -1)                   # row-major strict lower: (1,0), (2,0), (2,1), ...
+    k = i * (i - 1) // 2 + j
+    assert np.array_equal(k, np.arange(k.size))
+    pos = n * j - j * (j + 1) // 2 + (i - j - 1)     # pdist's index of the pair (j, i)
+    assert np.allclose(got, ref[pos], rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("n,bits,rmax", [(2, 4, 8), (33, 6, 20), (100, 10, 64), (257, 12, 2048)])
+def test_collide_strict_matches_brute_force(n, bits, rmax):
+    c, r = synth.spheres(n, seed=90 + n, coord_bits=bits, rmin=0, rmax=rmax)
+    words = oracle.collide_strict(c, r)
+    total = n * (n - 1) // 2
+    assert words.size == -(-total // 32)
+    flags = np.unpackbits(words.view(np.uint8), bitorder="little")
+    assert not flags[total:].any()                   # unused bits of the last word are zero
+    i, j = np.tril_indices(n, -1)
+    assert np.array_equal(flags[:total].astype(bool), _brute_collisions(c, r)[i, j])
