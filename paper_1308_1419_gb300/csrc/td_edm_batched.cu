@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(edm_tile_threads(RHO), edm_tile_min_ctas(RHO))
         const BatchMeta m = meta[lo];
         uint32_t bi, bj;
         ltm_g(u - P[lo], bi, bj);
-        Tile::run(x + m.x_off, m.n, m.d, bi * RHO, bj * RHO, out + m.out_off, sm);
+        Tile::template run<true>(x + m.x_off, m.n, m.d, bi * RHO, bj * RHO, out + m.out_off, sm);
     }
 }
 

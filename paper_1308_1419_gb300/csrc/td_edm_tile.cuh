@@ -5,9 +5,10 @@
 // and rho column points are staged in shared memory by asynchronous copies, KC features at a
 // time, double-buffered (chunk c + 1 loads while chunk c is consumed); each thread keeps a
 // TM x TN register tile of partial sums.  Two staging layouts:
-//   point-major (d a multiple of 4 and 16-byte aligned points): 16-byte copies of 4 features of
-//     one point, rows padded to KC + 4 floats; a thread reads 4 features of a point per 128-bit
-//     shared load and applies them to its tile in feature order;
+//   point-major (d a multiple of 4): 16-byte copies of 4 features of one point, rows padded to
+//     KC + 4 floats; a thread reads 4 features of a point per 128-bit shared load (two, and a
+//     register shift, when the points start off a 16-byte boundary) and applies them to its tile
+//     in feature order;
 //   feature-major (any d, and the X2 form): 4-byte copies into one plane per feature, a feature
 //     step being a few 128-bit shared loads of TM row and TN column values.
 // With X2, two columns go through each packed sub.rn.f32x2 / fma.rn.f32x2 (sm_100+), which
@@ -113,23 +114,58 @@ struct EdmTile {
         cp_async_commit();
     }
 
-    // Point-major staging of features [k0, k0 + kc) (kc a multiple of 4): point r's 4-feature group
-    // f goes to row r, floats 4f .. 4f + 3, of the row (A) or column (B) plane.
+    // Point-major staging of features [k0, k0 + kc) (kc a multiple of 4).  The points sit DELTA
+    // floats past a 16-byte boundary (the same for every point, d being a multiple of 4), so the
+    // copies take the aligned 16-byte groups from feature k0 - DELTA on: feature k0 + kk of point r
+    // lands at float DELTA + kk of row r of the row (A) or column (B) plane.  A group's bytes past
+    // the point's last feature are not read (zero-filled); the DELTA floats before feature 0 of a
+    // point belong to the preceding point or problem of the same input array.
+    template <int DELTA>
     __device__ static __forceinline__ void stage_pm(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0,
                                                     uint32_t j0, bool diag, uint32_t k0, int kc, float *buf)
     {
         float *sA = buf, *sB = buf + RHO * PLD;
-        for (int e = threadIdx.x; e < RHO * (KC / 4); e += NT) {
-            const int r = e / (KC / 4), f = e % (KC / 4);
-            if (4 * f >= kc) continue;
-            const uint32_t i = i0 + r, j = j0 + r, k = k0 + 4 * f;
-            cp_async16(sA + r * PLD + 4 * f, i < n ? x + uint64_t(i) * d + k : x, i < n ? 16u : 0u);
-            if (!diag) cp_async16(sB + r * PLD + 4 * f, j < n ? x + uint64_t(j) * d + k : x, j < n ? 16u : 0u);
+        if (DELTA == 0) {
+            for (int e = threadIdx.x; e < RHO * (KC / 4); e += NT) {
+                const int r = e / (KC / 4), f = e % (KC / 4);
+                if (4 * f >= kc) continue;
+                const uint32_t i = i0 + r, j = j0 + r, k = k0 + 4 * f;
+                cp_async16(sA + r * PLD + 4 * f, i < n ? x + uint64_t(i) * d + k : x, i < n ? 16u : 0u);
+                if (!diag) cp_async16(sB + r * PLD + 4 * f, j < n ? x + uint64_t(j) * d + k : x, j < n ? 16u : 0u);
+            }
+        } else {
+            constexpr int G = KC / 4 + 1;  // 16-byte groups per point row
+            const int groups = (DELTA + kc + 3) / 4;
+            for (int e = threadIdx.x; e < RHO * G; e += NT) {
+                const int r = e / G, f = e % G;
+                if (f >= groups) continue;
+                const uint32_t k = k0 + 4 * f;  // the group holds features k - DELTA .. k - DELTA + 3
+                // bytes of the point from feature k - DELTA on (d + DELTA - k >= 1 for every used group)
+                const uint32_t bytes = min(16u, 4 * (d + DELTA - k));
+                const uint32_t i = i0 + r, j = j0 + r;
+                cp_async16(sA + r * PLD + 4 * f, i < n ? x + uint64_t(i) * d + k - DELTA : x, i < n ? bytes : 0u);
+                if (!diag)
+                    cp_async16(sB + r * PLD + 4 * f, j < n ? x + uint64_t(j) * d + k - DELTA : x, j < n ? bytes : 0u);
+            }
         }
         cp_async_commit();
     }
 
+    // Four consecutive features of a staged point row: the aligned group at float offset `at` of
+    // the plane, shifted DELTA floats into the next group.
+    template <int DELTA>
+    __device__ static __forceinline__ float4 features4(const float *plane, int at)
+    {
+        const float4 lo = *reinterpret_cast<const float4 *>(plane + at);
+        if (DELTA == 0) return lo;
+        const float4 hi = *reinterpret_cast<const float4 *>(plane + at + 4);
+        if (DELTA == 1) return make_float4(lo.y, lo.z, lo.w, hi.x);
+        if (DELTA == 2) return make_float4(lo.z, lo.w, hi.x, hi.y);
+        return make_float4(lo.w, hi.x, hi.y, hi.z);
+    }
+
     // Point-major form of run(): the same sums, each accumulator taking features in order.
+    template <int DELTA>
     __device__ static void run_pm(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
                                   float *__restrict__ out, float *sm)
     {
@@ -141,14 +177,14 @@ struct EdmTile {
 #pragma unroll
             for (int b = 0; b < TN; ++b) acc[a][b] = 0.0f;
         const uint32_t nchunks = (d + KC - 1) / KC;
-        stage_pm(x, n, d, i0, j0, diag, 0, d < uint32_t(KC) ? int(d) : KC, sm);
+        stage_pm<DELTA>(x, n, d, i0, j0, diag, 0, d < uint32_t(KC) ? int(d) : KC, sm);
         for (uint32_t c = 0; c < nchunks; ++c) {
             const uint32_t k0 = c * KC;
             const int kc = d - k0 < uint32_t(KC) ? int(d - k0) : KC;
             if (c + 1 < nchunks) {
                 const uint32_t k1 = k0 + KC;
-                stage_pm(x, n, d, i0, j0, diag, k1, d - k1 < uint32_t(KC) ? int(d - k1) : KC,
-                         sm + ((c + 1) & 1) * STAGE_FLOATS);
+                stage_pm<DELTA>(x, n, d, i0, j0, diag, k1, d - k1 < uint32_t(KC) ? int(d - k1) : KC,
+                                sm + ((c + 1) & 1) * STAGE_FLOATS);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
@@ -159,10 +195,10 @@ struct EdmTile {
             for (int kk = 0; kk < kc; kk += 4) {
                 float4 av[TM];
 #pragma unroll
-                for (int a = 0; a < TM; ++a) av[a] = *reinterpret_cast<const float4 *>(A + (tr + RT * a) * PLD + kk);
+                for (int a = 0; a < TM; ++a) av[a] = features4<DELTA>(A, (tr + RT * a) * PLD + kk);
 #pragma unroll
                 for (int b = 0; b < TN; ++b) {
-                    const float4 bv = *reinterpret_cast<const float4 *>(B + (tc + CT * b) * PLD + kk);
+                    const float4 bv = features4<DELTA>(B, (tc + CT * b) * PLD + kk);
 #pragma unroll
                     for (int a = 0; a < TM; ++a) {
                         float t = av[a].x - bv.x;
@@ -179,6 +215,17 @@ struct EdmTile {
             __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
         }
         store(n, i0, j0, out, acc);
+    }
+
+    // The misaligned point-major bodies, kept out of line so that each gets its own register
+    // allocation instead of adding to the caller's.
+    __device__ static __noinline__ void run_pm_shifted(uint32_t delta, const float *__restrict__ x, uint32_t n,
+                                                       uint32_t d, uint32_t i0, uint32_t j0, float *__restrict__ out,
+                                                       float *sm)
+    {
+        if (delta == 1) run_pm<1>(x, n, d, i0, j0, out, sm);
+        else if (delta == 2) run_pm<2>(x, n, d, i0, j0, out, sm);
+        else run_pm<3>(x, n, d, i0, j0, out, sm);
     }
 
     __device__ static __forceinline__ void store(uint32_t n, uint32_t i0, uint32_t j0, float *__restrict__ out,
@@ -198,12 +245,20 @@ struct EdmTile {
         }
     }
 
-    // sm: SMEM_FLOATS floats.  All NT threads of the CTA call it together.
+    // sm: SMEM_FLOATS floats.  All NT threads of the CTA call it together.  ANY_ALIGN: the points
+    // may start at any 4-byte boundary of a larger array (the batched form's concatenated input);
+    // otherwise d % 4 == 0 implies 16-byte aligned points.
+    template <bool ANY_ALIGN = false>
     __device__ static void run(const float *__restrict__ x, uint32_t n, uint32_t d, uint32_t i0, uint32_t j0,
                                float *__restrict__ out, float *sm)
     {
         if (!X2 && d % 4 == 0 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
-            run_pm(x, n, d, i0, j0, out, sm);
+            run_pm<0>(x, n, d, i0, j0, out, sm);
+            return;
+        }
+        if (ANY_ALIGN && !X2 && d % 4 == 0) {
+            const uint32_t delta = static_cast<uint32_t>(reinterpret_cast<uintptr_t>(x) >> 2) & 3u;
+            run_pm_shifted(delta, x, n, d, i0, j0, out, sm);
             return;
         }
         run_fm(x, n, d, i0, j0, out, sm);
