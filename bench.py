@@ -26,7 +26,7 @@ sys.path.insert(0, ROOT)
 
 SIZES = [1024, 4096, 16384, 65536]
 RHOS = [8, 16, 32]
-STRATS = ["LTM", "BB", "UTM", "RB", "REC"]
+STRATS = ["LTM", "BB", "UTM", "RB", "REC", "UTM-BLOCK"]
 METRIC = "useful triangle pairs/s (g(lambda) probe sweep)"
 UNIT = "pairs/s"
 
@@ -249,7 +249,8 @@ def run_ours(args):
     # ---- compared strategies (same sweep), both schedules
     compare = {}
     for strategy in ([] if args.no_compare else STRATS):
-        for sched in (("chunked", "persistent", "grid") if strategy in ("LTM", "BB", "REC") else ("persistent", "grid")):
+        for sched in (("chunked", "persistent", "grid") if strategy in ("LTM", "BB", "REC", "UTM-BLOCK")
+                      else ("persistent", "grid")):
             csteps = max(3, min(20, args.steps // 2))
             cms, _, cper = timed(strategy, sched, csteps, 2, per_launch=True)
             compare[f"{strategy}/{sched}"] = {
@@ -299,9 +300,10 @@ def run_ours(args):
                 "algorithmic_bytes_per_launch": 4 * tri(65536)}
 
     # ---- end to end: the same sweep through the public API with the output in HOST memory.
-    # Two ways: (copy) the kernel writes device memory and the result is copied to pinned host
-    # memory; (direct) the kernel writes the pinned host buffer itself over the host link.  The
-    # faster one is reported; both are kept in the line.
+    # Three ways: (copy) the kernel writes device memory and the result is copied to pinned host
+    # memory; (direct) the kernel writes the pinned host buffer itself over the host link;
+    # (overlap) copies on a second stream overlap the next launch.  The fastest is reported; all
+    # are kept in the line.
     e2e = None
     if not args.no_e2e:
         host = torch.empty(tri(max(SIZES)), dtype=torch.int32, pin_memory=True)
@@ -319,8 +321,28 @@ def run_ours(args):
                 for rho in RHOS:
                     td.td_map_probe("LTM", args.sched, N, rho, host)
 
+        # (overlap) the kernel writes one of two device buffers while the previous result goes to
+        # pinned host memory on a copy stream: the host link (~190 GB/s here) is the bound
+        slots = [out, torch.empty_like(out)]
+        copy_stream = torch.cuda.Stream()
+        slot_free = [torch.cuda.Event(), torch.cuda.Event()]
+
+        def e2e_overlap():
+            k = 0
+            for N in SIZES:
+                for rho in RHOS:
+                    slot = slots[k % 2]
+                    stream.wait_event(slot_free[k % 2])
+                    td.td_map_probe("LTM", args.sched, N, rho, slot)
+                    copy_stream.wait_stream(stream)
+                    with torch.cuda.stream(copy_stream):
+                        host[: tri(N)].copy_(slot[: tri(N)], non_blocking=True)
+                        slot_free[k % 2].record(copy_stream)
+                    k += 1
+            stream.wait_stream(copy_stream)
+
         modes = {}
-        for name, fn in (("copy", e2e_copy), ("direct", e2e_direct)):
+        for name, fn in (("copy", e2e_copy), ("direct", e2e_direct), ("overlap", e2e_overlap)):
             fn()
             barrier()
             t0 = time.perf_counter()
@@ -360,6 +382,9 @@ def run_case(args):
     import torch
     from paper_1308_1419_gb300 import td
     from paper_1308_1419_gb300 import synth
+    for opt in args.opt:
+        name, value = opt.split("=")
+        td.td_set_option(name, int(value))
     parts = args.case.split(":")
     kind, strategy, sched = (parts + ["", ""])[:3]
     if kind == "probe":
@@ -585,6 +610,8 @@ def main():
                     help="edm-features: the distance-map sweep of Sec. IV (N = 1024..30720, d = 1..4, rho 16, "
                          "all strategies under --sched); ltm-variants: the LTM implementations of Sec. III-A "
                          "against BB with the map-only dummy kernel; one JSON line")
+    ap.add_argument("--opt", action="append", default=[],
+                    help="library option for --case runs, name=value (edm_f32x2, probe_strip); repeatable")
     ap.add_argument("--case", default="sweep",
                     help="sweep (default), or one kernel alone: probe:<strategy>:<sched>:<N>:<rho>, "
                          "edm:<strategy>:<sched>:<n>:<d>:<rho>, collide:<strategy>:<sched>:<n>")
