@@ -36,8 +36,8 @@ UNIT = "pairs/s"
 # they change the roofline line reports traffic as null until a new capture is taken.
 PROBE_SOURCES = ("td_probe.cu", "td_tiles.cuh", "td_device.cuh", "td_strategies.cuh")
 PROBE_TRAFFIC = {
-    "sources_sha256": "3c8ee18f1721e7a9f14ec81fa2a2584544ddcdf96761e77466b20034b804dee7",
-    "bytes_per_launch": {8: 8540588288, 16: 8544222208, 32: 8546744064},
+    "sources_sha256": "b7e4bb1258903cf7785774dd196da472d3d97f517876b66a5c086eb976e27b54",
+    "bytes_per_launch": {8: 8540754432, 16: 8545035264, 32: 8547230976},
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
                "-k regex:k_probe_chunked -s 3 -c 1 "
                "python bench.py --case probe:LTM:chunked:65536:<rho> --steps 1 --warmup 3",

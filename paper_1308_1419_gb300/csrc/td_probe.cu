@@ -69,7 +69,30 @@ __device__ __forceinline__ uint4 probe4(uint32_t key)
                       splitmix32_mulshift(key + 3));
 }
 
-template <class Tiles, int RHO>
+// The chunk of 4 elements starting at row-local j of row i (flat T(i) + j, a multiple of 4).
+__device__ __forceinline__ void probe_chunk(uint32_t *__restrict__ out, uint32_t N, uint32_t i, uint64_t ti,
+                                            uint32_t j)
+{
+    if (j + 3 <= i) {
+        __stcs(reinterpret_cast<uint4 *>(out + ti + j), probe4(i * N + j));
+    } else {  // the chunk runs past the end of row i into the next row(s)
+        uint32_t ii = i;
+        uint64_t tii = ti;
+        for (uint32_t k = 0; k < 4; ++k) {
+            const uint64_t P = ti + j + k;
+            while (P > tii + ii) {
+                tii += ii + 1;
+                ++ii;
+            }
+            if (ii >= N) break;
+            out[P] = splitmix32_mulshift(ii * N + static_cast<uint32_t>(P - tii));
+        }
+    }
+}
+
+// CPL > 0: strips at most 128 CPL elements wide, each lane's chunks of a row in a fully unrolled
+// loop; CPL = 0: any width, a runtime loop (the wide strips of large launches).
+template <class Tiles, int RHO, int CPL>
 __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t S, uint32_t *__restrict__ out)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -89,26 +112,18 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
                 if (i >= N) break;
                 const uint32_t jhi = min((bj + run) * RHO, i + 1);  // row-local end (exclusive)
                 const uint64_t ti = tri(i);
-                uint32_t *row = out + ti;
                 // first row-local j >= jlo whose flat index T(i) + j is a multiple of 4
                 const uint32_t c0 = jlo + ((4u - ((static_cast<uint32_t>(ti) + jlo) & 3u)) & 3u);
-#pragma unroll 2
-                for (uint32_t j = c0 + 4 * lane; j < jhi; j += 128) {
-                    if (j + 3 <= i) {
-                        __stcs(reinterpret_cast<uint4 *>(row + j), probe4(i * N + j));
-                    } else {  // the chunk runs past the end of row i into the next row(s)
-                        uint32_t ii = i;
-                        uint64_t tii = ti;
-                        for (uint32_t k = 0; k < 4; ++k) {
-                            const uint64_t P = ti + j + k;
-                            while (P > tii + ii) {
-                                tii += ii + 1;
-                                ++ii;
-                            }
-                            if (ii >= N) break;
-                            out[P] = splitmix32_mulshift(ii * N + static_cast<uint32_t>(P - tii));
-                        }
+                if (CPL > 0) {
+#pragma unroll
+                    for (int c = 0; c < CPL; ++c) {
+                        const uint32_t j = c0 + 4 * (lane + 32 * c);
+                        if (j >= jhi) break;
+                        probe_chunk(out, N, i, ti, j);
                     }
+                } else {
+#pragma unroll 2
+                    for (uint32_t j = c0 + 4 * lane; j < jhi; j += 128) probe_chunk(out, N, i, ti, j);
                 }
             }
         }
@@ -126,9 +141,11 @@ template <class Tiles, int RHO>
 td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
 {
     if (t.units == 0) return TD_OK;
-    auto k = k_probe_chunked<Tiles, RHO>;
-    const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, ~0ull) * 8;
-    const uint32_t S = chunked_strip_width(t.units, RHO, resident, kStripMax, 8192) / RHO;
+    auto wide = k_probe_chunked<Tiles, RHO, 0>;
+    auto narrow = k_probe_chunked<Tiles, RHO, 2>;
+    const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(wide), 256, 0, ~0ull) * 8;
+    const uint32_t W = chunked_strip_width(t.units, RHO, resident, kStripMax, 8192), S = W / RHO;
+    const auto k = W <= 256 ? narrow : wide;
     const uint64_t strips = (t.units + S - 1) / S;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (strips + 7) / 8);
     k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, S, out);
