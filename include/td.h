@@ -218,7 +218,7 @@ size_t td_edm_gram_workspace(uint32_t n, uint32_t d);
  * norms in FP32 from the FP32 points.  A pair whose D^2 falls below 1e-2 (|x_i|^2 + |x_j|^2)
  * (the diagonal included) is recomputed in the direct FP32 form sum_k (x_i[k] - x_j[k])^2, since
  * the Gram subtraction cancels there.  Other pairs carry the BF16 error of the inner product.
- * Same output layout as td_edm.  x: device, float[n][d], d a multiple of 8 in [8, 256], 16-byte
+ * Same output layout as td_edm.  x: device, float[n][d], d a multiple of 8 in [8, 8192], 16-byte
  * aligned; out: device, float[T(n)], 16-byte aligned; ws: device, td_edm_gram_workspace(n, d)
  * bytes, 1024-byte aligned.  Asynchronous; the pipeline's waits are bounded, and a wait that
  * runs out is reported by td_edm_gram_status. */

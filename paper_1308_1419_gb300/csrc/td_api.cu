@@ -354,8 +354,8 @@ td_status td_edm_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
 {
     g_err[0] = 0;
     if (n == 0) return TD_OK;
-    if (d == 0 || d % 8 != 0 || d > 256)
-        return fail(TD_ERR_UNSUPPORTED, "td_edm_gram needs d a multiple of 8 in [8, 256] (got %u)", d);
+    if (d == 0 || d % 8 != 0 || d > 8192)
+        return fail(TD_ERR_UNSUPPORTED, "td_edm_gram needs d a multiple of 8 in [8, 8192] (got %u)", d);
     if (!x || !out || !ws) return fail(TD_ERR_INVALID_ARG, "x, out and workspace must be non-NULL");
     if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
     if (reinterpret_cast<uintptr_t>(ws) & 1023u) return fail(TD_ERR_INVALID_ARG, "workspace must be 1024-byte aligned");

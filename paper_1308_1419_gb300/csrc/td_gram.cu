@@ -216,14 +216,21 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint32_t bi, bj;
             ltm_g(lam, bi, bj);
             const uint32_t a = uint32_t(t & 1), use = uint32_t(t >> 1);
+            // this warp's 32 x 32 chunk: rows i0 + lane (TMEM lanes 32 q ..), columns jb + cc.  The
+            // norms do not depend on the accumulator: their loads go out before the wait for it
+            // (the norms are zero-padded to whole blocks, so the 16-byte loads need no bounds)
+            const uint32_t i0 = bi * BM + 32 * q, i = i0 + lane, jb = bj * BM + c0;
+            const float ni = __ldg(norms + i);
+            float4 nq[8];
+            const float4 *nj4 = reinterpret_cast<const float4 *>(norms + jb);
+#pragma unroll
+            for (uint32_t c4 = 0; c4 < 8; ++c4) nq[c4] = __ldg(nj4 + c4);
             const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull_bar(a), use & 1u));
             if (!ready) {
                 if (lane == 0) fail_role(kErrEpilogue);
                 break;
             }
             tc_fence_after();
-            // this warp's 32 x 32 chunk: rows i0 + lane (TMEM lanes 32 q ..), columns jb + cc
-            const uint32_t i0 = bi * BM + 32 * q, i = i0 + lane, jb = bj * BM + c0;
             // interior: every row below n and every column left of every row (then also below n)
             const bool interior = bi > bj && i0 + 32 <= n;
             float v[32];
@@ -232,17 +239,13 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(a));
-            // D^2 = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j> and the cancellation test; the column norms
-            // arrive as broadcast 16-byte loads (the norms are zero-padded to whole blocks).  The
-            // sign of d2 - kCancel s2 is shifted into `neg` (column cc at bit 31 - cc).  A pair
-            // with d2 < 0 always cancels, so the NaN its square root gives is rewritten later.
-            const float ni = __ldg(norms + i);
-            const float4 *nj4 = reinterpret_cast<const float4 *>(norms + jb);
+            // D^2 = |x_i|^2 + |x_j|^2 - 2 <x_i, x_j> and the cancellation test.  The sign of
+            // d2 - kCancel s2 is shifted into `neg` (column cc at bit 31 - cc).  A pair with
+            // d2 < 0 always cancels, so the NaN its square root gives is rewritten later.
             uint32_t neg = 0;
 #pragma unroll
             for (uint32_t c4 = 0; c4 < 8; ++c4) {
-                const float4 nq = __ldg(nj4 + c4);
-                const float nj[4] = {nq.x, nq.y, nq.z, nq.w};
+                const float nj[4] = {nq[c4].x, nq[c4].y, nq[c4].z, nq[c4].w};
                 float w[4];
 #pragma unroll
                 for (uint32_t k = 0; k < 4; ++k) {

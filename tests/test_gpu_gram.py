@@ -41,7 +41,7 @@ def _check_pairs(xh, out, ii, jj):
     return float(rel.max()), float(np.sqrt((rel ** 2).mean()))
 
 
-@pytest.mark.parametrize("n,d", [(1, 8), (37, 8), (128, 64), (300, 64), (257, 200), (640, 256)])
+@pytest.mark.parametrize("n,d", [(1, 8), (37, 8), (128, 64), (300, 64), (257, 200), (640, 256), (300, 520), (200, 1024)])
 def test_gram_small_all_pairs(n, d):
     xh = synth.uniform_points(n, d, 7000 + n + d)
     xh[n // 3] = xh[n // 5]  # a duplicated point: distance exactly 0 through the recompute
@@ -82,9 +82,9 @@ def test_gram_rejects():
     x = torch.zeros(10, 12, device="cuda")
     with pytest.raises(td.TDError):
         td.td_edm_gram(x)                                  # d not a multiple of 8
-    x = torch.zeros(10, 264, device="cuda")
+    x = torch.zeros(10, 8200, device="cuda")
     with pytest.raises(td.TDError):
-        td.td_edm_gram(x)                                  # d > 256
+        td.td_edm_gram(x)                                  # d > 8192
 
 
 def test_gram_queue_overflow_identical_points():
