@@ -46,6 +46,22 @@ int sm_count()
     return n;
 }
 
+td_status set_dynamic_smem_once(const void *kernel, size_t bytes)
+{
+    static std::mutex mu;
+    static std::unordered_map<uint64_t, size_t> done;  // key: device ^ kernel address
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint64_t key = reinterpret_cast<uint64_t>(kernel) ^ (uint64_t(dev) << 56);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return TD_OK;
+    const td_status s = cuda_status(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)),
+                                    "dynamic shared memory attribute");
+    if (s == TD_OK) done[key] = bytes;
+    return s;
+}
+
 uint64_t persistent_ctas(const void *kernel, int threads, size_t smem, uint64_t units)
 {
     static std::mutex mu;

@@ -136,8 +136,7 @@ td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, f
     auto k = k_edm_chunked<Tiles, RHO, D>;
     const uint32_t wmax = edm_chunk_wmax(d);
     const size_t smax = edm_chunk_smem(d, wmax);
-    td_status s = cuda_status(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smax)),
-                              "td_edm chunked shared memory attribute");
+    td_status s = set_dynamic_smem_once(reinterpret_cast<const void *>(k), smax);
     if (s != TD_OK) return s;
     const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smax, ~0ull) * kWarps;
     const uint32_t w = chunked_strip_width(t.units, RHO, resident, wmax, wmax);

@@ -427,8 +427,7 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
-    s = cuda_status(cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES),
-                    "td_edm_gram shared memory attribute");
+    s = set_dynamic_smem_once(reinterpret_cast<const void *>(k_gram), SMEM_BYTES);
     if (s != TD_OK) return s;
     const uint32_t nt = (n + BM - 1) / BM;
     const uint64_t tiles = tri(nt);

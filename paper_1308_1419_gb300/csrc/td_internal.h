@@ -20,6 +20,9 @@ int sm_count();
 // Persistent grid for a kernel: SM count x resident CTAs per SM (cached per device/kernel),
 // capped at `units` (at least 1).
 uint64_t persistent_ctas(const void *kernel, int threads, size_t smem, uint64_t units);
+// Raises a kernel's dynamic shared memory limit to `bytes` on the current device, once: later
+// calls (a stream capture among them) make no CUDA call.
+td_status set_dynamic_smem_once(const void *kernel, size_t bytes);
 
 // Launch space of a strategy (host closed forms; mirrors what the launchers issue).
 struct Plan {
