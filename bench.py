@@ -417,22 +417,32 @@ def run_case(args):
         def call():
             td.td_collide(strategy, sched, ct, rt, table)
     elif kind == "edmstrict":
-        # edmstrict:<n>:<d>: strict-lower distance map, element-level strict g
+        # edmstrict:<n>:<d>[:<strategy>:<rho>]: strict-lower distance map, element-level strict g,
+        # or (with a strategy) mapped at the block level over the triangle of side n - 1
         n, d = int(strategy), int(sched)
         x = torch.from_numpy(synth.uniform_points(n, d, synth.seed_for(1))).cuda()
         out = torch.empty(max(n * (n - 1) // 2, 4), dtype=torch.float32, device="cuda")
         pairs, nbytes = n * (n - 1) // 2, 4 * (n * (n - 1) // 2)
-        def call():
-            td.td_edm_strict(x, out)
+        if len(parts) > 4:
+            def call():
+                td.td_edm_strict_blocks(parts[3], x, int(parts[4]), out)
+        else:
+            def call():
+                td.td_edm_strict(x, out)
     elif kind == "collidestrict":
-        # collidestrict:<n>: strict-lower collision bits, element-level strict g
+        # collidestrict:<n>[:<strategy>:<rho>]: strict-lower collision bits, element-level strict g,
+        # or (with a strategy) mapped at the block level
         n = int(strategy)
         c, r = synth.spheres(n)
         ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
         bits = torch.empty(max(td.td_collide_strict_words(n), 4), dtype=torch.int32, device="cuda")
         pairs, nbytes = n * (n - 1) // 2, 4 * td.td_collide_strict_words(n)
-        def call():
-            td.td_collide_strict(ct, rt, bits)
+        if len(parts) > 3:
+            def call():
+                td.td_collide_strict_blocks(parts[2], ct, rt, int(parts[3]), bits)
+        else:
+            def call():
+                td.td_collide_strict(ct, rt, bits)
     elif kind == "gram":
         # gram:<n>:<d>: BF16 tensor-core Gram form with FP32 direct recompute
         n, d = int(strategy), int(sched)

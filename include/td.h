@@ -191,6 +191,22 @@ uint64_t td_collide_strict_words(uint32_t n); /* ceil(n(n-1)/2 / 32) */
 td_status td_edm_strict(const float *x, uint32_t n, uint32_t d, float *out, void *stream);
 td_status td_collide_strict(const int32_t *centers, const int32_t *radii, uint32_t n, uint32_t *bits, void *stream);
 
+/* The same two strict outputs (same layout, bit-identical) mapped at the block level, the fast
+ * form: the pairs (i, j), j < i < n, packed at i(i-1)/2 + j, are the with-diagonal packed
+ * triangle of side n - 1 whose row i' holds the pairs of point i' + 1 (pair (i' + 1, j) at
+ * T(i') + j, j <= i').  Its rho x rho blocks are issued by g(lambda) (m = TD_MAP_LTM) or by BB
+ * (TD_MAP_BB) under the chunked schedule: warps walk strips of consecutive blocks of a block row
+ * and write aligned 16-byte chunks (distances) or whole 32-bit words (collision bits, one
+ * __ballot_sync per word).  rho: 8, 16 or 32.  stats (host, may be NULL): the block counts of
+ * the triangle of side n - 1.
+ * td_edm_strict_blocks: 1 <= d <= 8 (larger d: td_edm_strict); x and out 16-byte aligned.
+ * td_collide_strict_blocks: centers, radii and bits 4-byte aligned.
+ * n < 2: no-op.  Other errors as td_edm_strict / td_collide_strict. */
+td_status td_edm_strict_blocks(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
+                               td_launch_stats *stats, void *stream);
+td_status td_collide_strict_blocks(td_mapping m, const int32_t *centers, const int32_t *radii, uint32_t n,
+                                   uint32_t rho, uint32_t *bits, td_launch_stats *stats, void *stream);
+
 /* Collision table (collision detection is a td-problem named in the abstract and Sec. I):
  * spheres i > j collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, decided exactly.  The table is
  * bit-packed in 32 x 32 bit-tiles over the tile triangle of side nt = ceil(n / 32): tile

@@ -182,6 +182,14 @@ static void fill_stats(td_launch_stats *st, const Plan &p, uint64_t ctas)
     st->ctas = ctas;
 }
 
+// The strict lower triangle of n points as the with-diagonal triangle of side n - 1.
+static td_status plan_strict_blocks(td_mapping m, uint32_t n, uint32_t rho, Plan &p)
+{
+    if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "the block-mapped strict forms serve LTM and BB");
+    if (rho != 8 && rho != 16 && rho != 32) return fail(TD_ERR_INVALID_ARG, "the block-mapped strict forms need rho 8, 16 or 32 (got %u)", rho);
+    return plan_strategy(m, TD_SCHED_CHUNKED, n < 2 ? 0 : n - 1, rho, p);
+}
+
 }  // namespace td
 
 using namespace td;
@@ -300,7 +308,7 @@ td_status td_edm(td_mapping m, td_schedule sched, const float *x, uint32_t n, ui
     if (sched == TD_SCHED_CHUNKED && rho > 32)
         return fail(TD_ERR_UNSUPPORTED, "the chunked distance map needs rho 8, 16 or 32 (rho 64/128 is the tiled body)");
     if (sched == TD_SCHED_CHUNKED)
-        st = launch_edm_chunked(m, x, n, d, rho, out, p, cs, &ctas);
+        st = launch_edm_chunked(m, x, n, d, rho, out, p, false, cs, &ctas);
     else
         st = rho <= 32 ? launch_edm_pair(m, sched, x, n, d, rho, out, p, cs, &ctas)
                        : launch_edm_tiled(m, sched, x, n, d, rho, out, p, option(TD_OPT_EDM_F32X2) != 0, cs, &ctas);
@@ -362,6 +370,48 @@ td_status td_collide_strict(const int32_t *centers, const int32_t *radii, uint32
     if ((reinterpret_cast<uintptr_t>(centers) | reinterpret_cast<uintptr_t>(radii) | reinterpret_cast<uintptr_t>(bits)) & 3u)
         return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be 4-byte aligned");
     return launch_collide_strict(centers, radii, n, bits, static_cast<cudaStream_t>(stream));
+}
+
+
+td_status td_edm_strict_blocks(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
+                               td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    Plan p;
+    td_status st = td::plan_strict_blocks(m, n, rho, p);
+    if (st != TD_OK) return st;
+    if (d == 0) return fail(TD_ERR_INVALID_ARG, "d must be at least 1");
+    if (d > 8) return fail(TD_ERR_UNSUPPORTED, "td_edm_strict_blocks serves d <= 8 (got %u); use td_edm_strict", d);
+    if (n < 2) {
+        fill_stats(stats, p, 0);
+        return TD_OK;
+    }
+    if (!x || !out) return fail(TD_ERR_INVALID_ARG, "x and out must be non-NULL");
+    if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
+    uint64_t ctas = 0;
+    st = launch_edm_chunked(m, x, n, d, rho, out, p, true, static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
+}
+
+td_status td_collide_strict_blocks(td_mapping m, const int32_t *centers, const int32_t *radii, uint32_t n,
+                                   uint32_t rho, uint32_t *bits, td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    Plan p;
+    td_status st = td::plan_strict_blocks(m, n, rho, p);
+    if (st != TD_OK) return st;
+    if (n < 2) {
+        fill_stats(stats, p, 0);
+        return TD_OK;
+    }
+    if (!centers || !radii || !bits) return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be non-NULL");
+    if ((reinterpret_cast<uintptr_t>(centers) | reinterpret_cast<uintptr_t>(radii) | reinterpret_cast<uintptr_t>(bits)) & 3u)
+        return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be 4-byte aligned");
+    uint64_t ctas = 0;
+    st = launch_collide_chunked(m, centers, radii, n, rho, bits, p, static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
 }
 
 size_t td_edm_gram_workspace(uint32_t n, uint32_t d) { return gram_workspace_bytes(n, d); }

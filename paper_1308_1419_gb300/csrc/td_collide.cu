@@ -36,12 +36,6 @@ namespace {
 
 constexpr int kWarps = 8;
 
-__device__ __forceinline__ bool small_coords(const int4 &p)
-{
-    const int32_t lim = 1 << 23;
-    return p.x > -lim && p.x < lim && p.y > -lim && p.y < lim && p.z > -lim && p.z < lim;
-}
-
 template <class Tiles, bool P>
 __global__ void __launch_bounds__(32 * kWarps)
     k_collide(Tiles tiles, const int32_t *__restrict__ c, const int32_t *__restrict__ rad, uint32_t n,
@@ -53,7 +47,6 @@ __global__ void __launch_bounds__(32 * kWarps)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t first = uint64_t(blockIdx.x) * kWarps + warp;
     const uint64_t stride = P ? uint64_t(gridDim.x) * kWarps : tiles.units;
-    constexpr float kTol = 0x1p-20f;
     for (uint64_t u = first; u < tiles.units; u += stride) {
         uint32_t bi, bj;
         if (!tiles(u, bi, bj)) continue;  // warp-uniform
@@ -73,13 +66,10 @@ __global__ void __launch_bounds__(32 * kWarps)
             bool band = false;
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
-                const float4 p = rowsf[warp][r];
-                const float dx = p.x - fj.x, dy = p.y - fj.y, dz = p.z - fj.z;
-                const float s = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float R = p.w + fj.w, R2 = R * R;
-                const float diff = s - R2;
-                band = band || fabsf(diff) <= R2 * kTol;
-                const uint32_t b = __ballot_sync(0xffffffffu, diff <= 0.0f);
+                bool near;
+                const bool hit = collide_f32(rowsf[warp][r], fj, near);
+                band = band || near;
+                const uint32_t b = __ballot_sync(0xffffffffu, hit);
                 if (lane == 0) words[warp][r] = b;
             }
             exact = __any_sync(0xffffffffu, band);

@@ -73,6 +73,28 @@ __device__ __forceinline__ bool collide_exact(const int4 &p, const int4 &q)
     return dx * dx + dy * dy + dz * dz <= R * R;
 }
 
+// The same predicate on the FP32 pipe, for coordinates in (-2^23, 2^23) (small_coords) carried
+// as floats: coordinate differences are then integers below 2^24 and exact in FP32, the sum of
+// squares s (one multiply, two FMAs) is within a factor (1 +- 3u) of the truth (u = 2^-24) and
+// R^2 (R exact) within (1 +- u).  Outside the relative band |s - R^2| <= 2^-20 R^2 the sign of
+// s - R^2 is therefore the exact answer; *band reports a pair inside it, which the caller must
+// decide again with collide_exact.
+__device__ __forceinline__ bool small_coords(const int4 &p)
+{
+    const int32_t lim = 1 << 23;
+    return p.x > -lim && p.x < lim && p.y > -lim && p.y < lim && p.z > -lim && p.z < lim;
+}
+
+__device__ __forceinline__ bool collide_f32(const float4 &p, const float4 &q, bool &band)
+{
+    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    const float s = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float R = p.w + q.w, R2 = R * R;
+    const float diff = s - R2;
+    band = fabsf(diff) <= R2 * 0x1p-20f;
+    return diff <= 0.0f;
+}
+
 // g(lambda) as a functor (the mapper the LTM kernels are written against).
 struct LtmExact {
     __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &i, uint32_t &j) const { ltm_g(lam, i, j); }

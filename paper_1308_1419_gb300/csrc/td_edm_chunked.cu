@@ -15,6 +15,12 @@
 // row i into the next row(s) is computed element by element from global memory (at most one
 // chunk per row).
 //
+// The same kernel serves the strict lower triangle (td-problems without the diagonal, Eq.
+// (theorem_nodiag) of Sec. II-A): its pairs (i, j), j < i < n, packed at i(i-1)/2 + j, form the
+// with-diagonal packed triangle of side n - 1 whose row i' holds the pairs of point i' + 1 -- so
+// the blocks of that triangle are mapped exactly as above and only the row point moves down by
+// one (SHIFT = 1).
+//
 // Summation order as in every EDM kernel of libtd: t = x_i[k] - x_j[k], s = fma(t, t, s) for
 // k = 0 .. d-1 from s = 0, then sqrtf -- bit-identical to td_edm_pair and the tiled kernels.
 #include "td_internal.h"
@@ -47,7 +53,9 @@ __device__ __forceinline__ float direct(const float *__restrict__ x, uint32_t d,
     return sqrtf(s);
 }
 
-template <class Tiles, int RHO, int D>
+// n: side of the packed triangle (the number of points minus SHIFT); row i of it pairs point
+// i + SHIFT with the points j <= i.
+template <class Tiles, int RHO, int D, int SHIFT>
 __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uint32_t n, uint32_t S, uint32_t sl,
                                                              const float *__restrict__ x, uint32_t d,
                                                              float *__restrict__ out)
@@ -88,7 +96,7 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
                 const uint32_t c0 = jlo + ((4u - ((static_cast<uint32_t>(ti) + jlo) & 3u)) & 3u);
                 float xi[D ? D : kMaxD];
 #pragma unroll
-                for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) xi[k] = (D || k < dd) ? __ldg(x + uint64_t(i) * dd + k) : 0.0f;
+                for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) xi[k] = (D || k < dd) ? __ldg(x + uint64_t(i + SHIFT) * dd + k) : 0.0f;
                 for (uint32_t jb = c0; jb < jhi; jb += 128) {
 #pragma unroll
                     for (uint32_t m = 0; m < 4; ++m) {
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
                                     ++ii;
                                 }
                                 if (ii >= n) break;
-                                out[P] = direct<D>(x, d, ii, static_cast<uint32_t>(P - tii));
+                                out[P] = direct<D>(x, d, ii + SHIFT, static_cast<uint32_t>(P - tii));
                             }
                         }
                     }
@@ -128,12 +136,12 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
     }
 }
 
-template <class Tiles, int RHO, int D>
+template <class Tiles, int RHO, int D, int SHIFT = 0>
 td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st,
                        uint64_t *ctas)
 {
     if (t.units == 0) return TD_OK;
-    auto k = k_edm_chunked<Tiles, RHO, D>;
+    auto k = k_edm_chunked<Tiles, RHO, D, SHIFT>;
     const uint32_t wmax = edm_chunk_wmax(d);
     const size_t smax = edm_chunk_smem(d, wmax);
     td_status s = set_dynamic_smem_once(reinterpret_cast<const void *>(k), smax);
@@ -150,9 +158,15 @@ td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, f
 }
 
 template <int RHO, int D>
-td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float *out, const Plan &p, cudaStream_t st,
-                     uint64_t *ctas)
+td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float *out, const Plan &p, bool strict,
+                     cudaStream_t st, uint64_t *ctas)
 {
+    if (strict) {  // the strict triangle of n points = the packed triangle of side n - 1, rows shifted
+        if (m == TD_MAP_LTM) return launch_tiles<tiles::Ltm, RHO, D, 1>(tiles::Ltm{tri(p.nb)}, x, n - 1, d, out, st, ctas);
+        if (m == TD_MAP_BB)
+            return launch_tiles<tiles::Bb, RHO, D, 1>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, x, n - 1, d, out, st, ctas);
+        return fail(TD_ERR_UNSUPPORTED, "the block-mapped strict distance map serves LTM and BB");
+    }
     switch (m) {
     case TD_MAP_LTM: return launch_tiles<tiles::Ltm, RHO, D>(tiles::Ltm{tri(p.nb)}, x, n, d, out, st, ctas);
     case TD_MAP_UTM_BLOCK:
@@ -176,12 +190,12 @@ td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float
 
 template <int D>
 td_status launch_d(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out, const Plan &p,
-                   cudaStream_t st, uint64_t *ctas)
+                   bool strict, cudaStream_t st, uint64_t *ctas)
 {
     switch (rho) {
-    case 8: return launch_rho<8, D>(m, x, n, d, out, p, st, ctas);
-    case 16: return launch_rho<16, D>(m, x, n, d, out, p, st, ctas);
-    case 32: return launch_rho<32, D>(m, x, n, d, out, p, st, ctas);
+    case 8: return launch_rho<8, D>(m, x, n, d, out, p, strict, st, ctas);
+    case 16: return launch_rho<16, D>(m, x, n, d, out, p, strict, st, ctas);
+    case 32: return launch_rho<32, D>(m, x, n, d, out, p, strict, st, ctas);
     default: return fail(TD_ERR_INVALID_ARG, "the chunked distance map needs rho 8, 16 or 32 (got %u)", rho);
     }
 }
@@ -189,16 +203,16 @@ td_status launch_d(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_
 }  // namespace
 
 td_status launch_edm_chunked(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
-                             const Plan &p, cudaStream_t st, uint64_t *ctas)
+                             const Plan &p, bool strict, cudaStream_t st, uint64_t *ctas)
 {
     if (d == 0 || d > kMaxD)
         return fail(TD_ERR_UNSUPPORTED, "the chunked distance map serves d <= %u (got %u); use rho 64/128", kMaxD, d);
     switch (d) {
-    case 1: return launch_d<1>(m, x, n, d, rho, out, p, st, ctas);
-    case 2: return launch_d<2>(m, x, n, d, rho, out, p, st, ctas);
-    case 3: return launch_d<3>(m, x, n, d, rho, out, p, st, ctas);
-    case 4: return launch_d<4>(m, x, n, d, rho, out, p, st, ctas);
-    default: return launch_d<0>(m, x, n, d, rho, out, p, st, ctas);
+    case 1: return launch_d<1>(m, x, n, d, rho, out, p, strict, st, ctas);
+    case 2: return launch_d<2>(m, x, n, d, rho, out, p, strict, st, ctas);
+    case 3: return launch_d<3>(m, x, n, d, rho, out, p, strict, st, ctas);
+    case 4: return launch_d<4>(m, x, n, d, rho, out, p, strict, st, ctas);
+    default: return launch_d<0>(m, x, n, d, rho, out, p, strict, st, ctas);
     }
 }
 

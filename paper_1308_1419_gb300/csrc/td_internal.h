@@ -37,14 +37,20 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
                        bool cover, const Plan &p, cudaStream_t st, uint64_t *ctas);
 // Strip width (elements of one packed row) of the chunked schedule: the widest power of two in
-// [256, wauto] leaving at least four strips per resident warp; below 256 (down to rho, one block
-// per strip) while there are fewer strips than resident warps; or the TD_OPT_PROBE_STRIP value
-// (capped at wlimit).  Never below rho.
+// [min(256, wauto), wauto] leaving at least four strips per resident warp; below that (down to
+// rho, one block per strip) while there are fewer strips than resident warps; or the
+// TD_OPT_PROBE_STRIP value (capped at wlimit).  Never below rho.
 uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit);
 td_status launch_edm_strict(const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st);
 td_status launch_collide_strict(const int32_t *c, const int32_t *r, uint32_t n, uint32_t *bits, cudaStream_t st);
+// strict: the strict lower triangle of the n points, as the packed triangle of side n - 1 whose
+// row i' pairs point i' + 1 with j <= i' (p planned for side n - 1; LTM and BB).
 td_status launch_edm_chunked(td_mapping m, const float *x, uint32_t n, uint32_t d, uint32_t rho, float *out,
-                             const Plan &p, cudaStream_t st, uint64_t *ctas);
+                             const Plan &p, bool strict, cudaStream_t st, uint64_t *ctas);
+// Strict-lower collision bits under the chunked schedule of the block strategies (LTM, BB), p
+// planned for side n - 1.
+td_status launch_collide_chunked(td_mapping m, const int32_t *c, const int32_t *r, uint32_t n, uint32_t rho,
+                                 uint32_t *bits, const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_pair(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                           float *out, const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,

@@ -267,7 +267,7 @@ td_status launch_variant(td_mapping m, bool P, uint32_t N, uint32_t rho, Body bo
 uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit)
 {
     const int forced = option(TD_OPT_PROBE_STRIP);
-    uint32_t w = 256;
+    uint32_t w = wauto < 256 ? wauto : 256;
     if (forced > 0) {
         w = uint32_t(forced) < wlimit ? uint32_t(forced) : wlimit;
     } else {

@@ -82,6 +82,8 @@ _c_map_dummy = _sig("td_map_dummy", _int, _int, _int, _u32, _u32, _vp, _vp, _vp)
 _c_collide_strict_words = _sig("td_collide_strict_words", _u64, _u32)
 _c_edm_strict = _sig("td_edm_strict", _int, _vp, _u32, _u32, _vp, _vp)
 _c_collide_strict = _sig("td_collide_strict", _int, _vp, _vp, _u32, _vp, _vp)
+_c_edm_strict_blocks = _sig("td_edm_strict_blocks", _int, _int, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
+_c_collide_strict_blocks = _sig("td_collide_strict_blocks", _int, _int, _vp, _vp, _u32, _u32, _vp, _stats_p, _vp)
 
 
 def _check(status):
@@ -208,6 +210,36 @@ def td_collide_strict(centers: torch.Tensor, radii: torch.Tensor, bits: torch.Te
     bp = _dev(bits, torch.int32, words, "bits")
     _check(_c_collide_strict(cp, rp, n, bp, _stream(stream)))
     return bits
+
+
+def td_edm_strict_blocks(mapping, x: torch.Tensor, rho: int, out: torch.Tensor = None, stream=None):
+    """td_edm_strict's output mapped at the block level (LTM or BB, rho 8/16/32, d <= 8), and stats."""
+    if x.dim() != 2:
+        raise ValueError("x must be a 2-D (n, d) tensor")
+    n, d = x.shape
+    xp = _dev(x, torch.float32, n * d, "x")
+    total = n * (n - 1) // 2
+    if out is None:
+        out = torch.empty(max(total, 4), dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, total, "out")
+    st = td_launch_stats()
+    _check(_c_edm_strict_blocks(_mapping(mapping), xp, n, d, rho, op, C.byref(st), _stream(stream)))
+    return out, st.as_dict()
+
+
+def td_collide_strict_blocks(mapping, centers: torch.Tensor, radii: torch.Tensor, rho: int = 32,
+                             bits: torch.Tensor = None, stream=None):
+    """td_collide_strict's bits mapped at the block level (LTM or BB, rho 8/16/32), and stats."""
+    n = radii.numel()
+    cp = _dev(centers, torch.int32, 3 * n, "centers")
+    rp = _dev(radii, torch.int32, n, "radii")
+    words = td_collide_strict_words(n)
+    if bits is None:
+        bits = torch.empty(max(words, 4), dtype=torch.int32, device=radii.device)
+    bp = _dev(bits, torch.int32, words, "bits")
+    st = td_launch_stats()
+    _check(_c_collide_strict_blocks(_mapping(mapping), cp, rp, n, rho, bp, C.byref(st), _stream(stream)))
+    return bits, st.as_dict()
 
 
 def td_edm(mapping, schedule, x: torch.Tensor, rho: int, out: torch.Tensor = None, stream=None):

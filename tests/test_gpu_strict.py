@@ -80,3 +80,88 @@ def test_strict_errors_and_no_ops():
     assert td.td_collide_strict_words(0) == 0 and td.td_collide_strict_words(2) == 1
     assert td.td_collide_strict_words(33) == -(-33 * 32 // 2 // 32)
     td.td_edm_strict(x)
+
+
+# ---- the block-mapped strict forms: the strict triangle of n points as the packed triangle of
+# side n - 1 (row i' pairs point i' + 1 with j <= i'), blocks issued by g(lambda) or BB
+
+
+@pytest.mark.parametrize("mapping", ["LTM", "BB"])
+@pytest.mark.parametrize("rho", [8, 16, 32])
+def test_edm_strict_blocks_bit_identical(mapping, rho):
+    for d in (1, 2, 3, 4, 5, 8):
+        for n in (2, 3, 9, 33, 100, 517, 1000, 2049):
+            xh = synth.uniform_points(n, d, 900 + n + d)
+            x = torch.from_numpy(xh).cuda()
+            total = n * (n - 1) // 2
+            got, st = td.td_edm_strict_blocks(mapping, x, rho)
+            ref = td.td_edm_strict(x)
+            assert torch.equal(got[:total].view(torch.int32), ref[:total].view(torch.int32)), (mapping, rho, d, n)
+            nb = -(-(n - 1) // rho)
+            assert st["useful_blocks"] == nb * (nb + 1) // 2
+            if n in (100, 1000):
+                _check_rel(got[:total].cpu().numpy(), oracle.edm_strict(xh), (mapping, rho, d, n))
+
+
+def test_edm_strict_blocks_large_sampled():
+    n, d = 32768, 3
+    xh = synth.uniform_points(n, d, 4243)
+    x = torch.from_numpy(xh).cuda()
+    got, _ = td.td_edm_strict_blocks("LTM", x, 16)
+    ref = td.td_edm_strict(x)
+    total = n * (n - 1) // 2
+    assert torch.equal(got[:total].view(torch.int32), ref[:total].view(torch.int32))
+
+
+@pytest.mark.parametrize("mapping", ["LTM", "BB"])
+@pytest.mark.parametrize("rho", [8, 16, 32])
+def test_collide_strict_blocks_matches_oracle(mapping, rho):
+    for n, bits, rmax in [(2, 4, 8), (3, 4, 8), (33, 6, 20), (34, 6, 20), (100, 10, 64), (1000, 12, 256),
+                          (3001, 14, 2048)]:
+        c, r = synth.spheres(n, seed=800 + n + rho, coord_bits=bits, rmin=0, rmax=rmax)
+        got, st = td.td_collide_strict_blocks(mapping, torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda(), rho)
+        words = td.td_collide_strict_words(n)
+        assert np.array_equal(got[:words].cpu().numpy().view(np.uint32), oracle.collide_strict(c, r)), (mapping, rho, n)
+
+
+def test_collide_strict_blocks_exact_paths():
+    """Exactly touching pairs (the FP32 band) and coordinates beyond 2^23 (the integer path)."""
+    c = np.array([[0, 0, 0], [300, 400, 0], [0, 0, 0], [301, 400, 0],
+                  [-2**30, -2**30, -2**30], [2**30 - 1, 2**30 - 1, 2**30 - 1],
+                  [5, 5, 5], [5 + 16384 * 2, 5, 5]], dtype=np.int32)
+    r = np.array([200, 300, 200, 300, 16384, 16384, 16384, 16384], dtype=np.int32)
+    c = np.tile(c, (40, 1))
+    r = np.tile(r, 40)
+    small = c[:, :] % 1000
+    for cc in (c, small.astype(np.int32)):
+        for rho in (8, 32):
+            got, _ = td.td_collide_strict_blocks("LTM", torch.from_numpy(cc).cuda(), torch.from_numpy(r).cuda(), rho)
+            words = td.td_collide_strict_words(len(r))
+            assert np.array_equal(got[:words].cpu().numpy().view(np.uint32), oracle.collide_strict(cc, r)), rho
+
+
+def test_collide_strict_blocks_workload():
+    """The collision workload (n = 32768): identical to the element-level strict bits."""
+    c, r = synth.spheres(32768)
+    ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+    words = td.td_collide_strict_words(32768)
+    ref = td.td_collide_strict(ct, rt)[:words]
+    for mapping, rho in (("LTM", 32), ("BB", 32), ("LTM", 16)):
+        got, _ = td.td_collide_strict_blocks(mapping, ct, rt, rho)
+        assert torch.equal(got[:words], ref), (mapping, rho)
+    assert np.array_equal(ref.cpu().numpy().view(np.uint32), oracle.collide_strict(c, r))
+
+
+def test_strict_blocks_errors_and_no_ops():
+    x = torch.zeros(10, 3, device="cuda")
+    c = torch.zeros(10, 3, dtype=torch.int32, device="cuda")
+    r = torch.zeros(10, dtype=torch.int32, device="cuda")
+    for bad in (("UTM", 16), ("RB", 16), ("LTM", 64), ("LTM", 12)):
+        with pytest.raises(td.TDError):
+            td.td_edm_strict_blocks(bad[0], x, bad[1])
+        with pytest.raises(td.TDError):
+            td.td_collide_strict_blocks(bad[0], c, r, bad[1])
+    with pytest.raises(td.TDError):
+        td.td_edm_strict_blocks("LTM", torch.zeros(10, 9, device="cuda"), 16)  # d > 8: td_edm_strict
+    td.td_edm_strict_blocks("LTM", torch.zeros(1, 3, device="cuda"), 16)
+    td.td_collide_strict_blocks("LTM", c[:1], r[:1], 32)
