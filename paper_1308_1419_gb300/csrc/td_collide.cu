@@ -17,16 +17,14 @@
 // 32-bit comparison equals the exact definition.
 //
 // Fast path on the FP32 pipe (full rate, where the integer ALU runs at half rate): when every
-// coordinate of the tile's 64 spheres lies in (-2^23, 2^23), coordinate differences are integers
-// below 2^24 and exact in FP32.  The sum of squares s, formed with one multiply and two FMAs, is
-// then within a factor (1 +- 3u) of the truth (u = 2^-24), and R^2 (R exact) within (1 +- u).
-// With a margin of 2^-20 = 16u, s - R^2 > 2^-20 R^2 proves "no collision" and s - R^2 <
-// -2^-20 R^2 proves "collision" (the subtraction adds at most one more rounding, well inside
-// the margin).  If any pair of a tile falls inside that band, the whole tile is redone with the
-// exact integer test above; tiles with larger coordinates use the integer test throughout.
-// The per-row bookkeeping is kept out of the row loop: each row's ballot is parked in shared
-// memory by lane 0, and the validity mask (columns and rows below n, j < i on the diagonal) is
-// applied once per word.
+// coordinate of the tile's 64 spheres lies in (-2^23, 2^23), coordinate differences are exact
+// in FP32, and s - R^2 = fma(-R, R, s) decides the pair unless it falls within one band for
+// the whole tile, 2^-20 Rmax^2 with Rmax the largest row radius plus the largest column radius
+// (collide_f32_banded gives the error bound).  If any pair of a tile falls inside the band, the
+// whole tile is redone with the exact integer test above; tiles with larger coordinates use the
+// integer test throughout.  The 32 row words stay in registers (a ballot result is the same in
+// every lane) and lane 0 writes the tile's 128 bytes; only diagonal and edge tiles apply the
+// validity mask (columns and rows below n, j < i on the diagonal).
 #include "td_device.cuh"
 #include "td_internal.h"
 #include "td_tiles.cuh"
@@ -43,7 +41,6 @@ __global__ void __launch_bounds__(32 * kWarps)
 {
     __shared__ int4 rows[kWarps][32];
     __shared__ float4 rowsf[kWarps][32];
-    __shared__ uint32_t words[kWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t first = uint64_t(blockIdx.x) * kWarps + warp;
     const uint64_t stride = P ? uint64_t(gridDim.x) * kWarps : tiles.units;
@@ -59,36 +56,41 @@ __global__ void __launch_bounds__(32 * kWarps)
         rows[warp][lane] = pi;
         rowsf[warp][lane] = make_float4(float(pi.x), float(pi.y), float(pi.z), float(pi.w));
         __syncwarp();
+        // the 32 row words, warp-uniform: word r = ballot of row 32 bi + r
+        uint32_t w[32];
         bool exact = !__all_sync(0xffffffffu, small_coords(pj) && small_coords(pi));
         if (!exact) {
-            // FP32 pass: one ballot per row, its word parked in shared memory by lane 0; a pair
-            // within the relative band 2^-20 of R^2 marks the tile for the exact pass
+            // FP32 pass; a pair within the tile's band marks the tile for the exact pass
+            const float rmax = float(__reduce_max_sync(0xffffffffu, uint32_t(pi.w)) +
+                                     __reduce_max_sync(0xffffffffu, uint32_t(pj.w)));
+            const float band_c = 0x1p-20f * rmax * rmax;
             bool band = false;
 #pragma unroll
             for (int r = 0; r < 32; ++r) {
                 bool near;
-                const bool hit = collide_f32(rowsf[warp][r], fj, near);
+                const bool hit = collide_f32_banded(rowsf[warp][r], fj, band_c, near);
                 band = band || near;
-                const uint32_t b = __ballot_sync(0xffffffffu, hit);
-                if (lane == 0) words[warp][r] = b;
+                w[r] = __ballot_sync(0xffffffffu, hit);
             }
             exact = __any_sync(0xffffffffu, band);
         }
         if (exact) {  // integer pass for the whole tile (large coordinates, or a pair in the band)
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-                const uint32_t b = __ballot_sync(0xffffffffu, collide_exact(rows[warp][r], pj));
-                if (lane == 0) words[warp][r] = b;
-            }
+#pragma unroll
+            for (int r = 0; r < 32; ++r) w[r] = __ballot_sync(0xffffffffu, collide_exact(rows[warp][r], pj));
         }
-        __syncwarp();
-        // lane r owns row 32 bi + r: keep columns below n, rows below n, and j < i on the diagonal
-        const uint32_t colmask = __ballot_sync(0xffffffffu, j < n);
-        const uint32_t rows_valid = n - 32 * bi >= 32 ? 32u : n - 32 * bi;
-        const uint32_t valid = uint32_t(lane) < rows_valid ? (colmask & (bi == bj ? ((1u << lane) - 1u) : ~0u)) : 0u;
-        const uint64_t t = tri(bi) + bj;
-        table[t * 32 + lane] = words[warp][lane] & valid;
-        __syncwarp();
+        // keep columns below n, rows below n, and j < i on the diagonal
+        if (bi == bj || 32 * bi + 32 > n) {
+            const uint32_t colmask = __ballot_sync(0xffffffffu, j < n);
+            const uint32_t rows_valid = n - 32 * bi >= 32 ? 32u : n - 32 * bi;
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                w[r] &= uint32_t(r) < rows_valid ? (colmask & (bi == bj ? ((1u << r) - 1u) : ~0u)) : 0u;
+        }
+        if (lane == 0) {  // the tile's 32 words: 128 contiguous bytes, 16-byte aligned
+            uint4 *dst = reinterpret_cast<uint4 *>(table + (tri(bi) + bj) * 32);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        }
     }
 }
 

@@ -20,8 +20,9 @@
 // memory.
 //
 // The predicate is collide_exact's.  When every coordinate of the run's spheres is below 2^23
-// in magnitude it is taken on the FP32 pipe (collide_f32), and a row with a pair inside the
-// FP32 band is decided again with the integer test (spheres reloaded, off the fast path);
+// in magnitude it is taken on the FP32 pipe (collide_f32_banded, one band for the run), and a row
+// with a pair inside the band is decided again with the integer test (spheres reloaded, off the
+// fast path);
 // otherwise the integer test decides every pair of the run.
 #include "td_internal.h"
 #include "td_tiles.cuh"
@@ -56,11 +57,12 @@ __device__ __forceinline__ bool crossing_bit(const int32_t *__restrict__ c, cons
 }
 
 // One run's element rows.  SMALL: cols hold the column spheres as floats (every coordinate of
-// the run below 2^23), else as integers (reinterpreted).  Every row decides all NG groups (the
+// the run below 2^23) and band_c is the run's FP32 band (collide_f32_banded), else cols hold the
+// integers (reinterpreted).  Every row decides all NG groups (the
 // groups past the row's last word are not stored): a loop without an exit lets the groups'
 // independent predicate chains overlap.
 template <int RHO, bool SMALL>
-__device__ __forceinline__ void run_rows(const float4 (&cols)[NG], uint32_t bi, uint32_t jlo, uint32_t span, uint32_t n1,
+__device__ __forceinline__ void run_rows(const float4 (&cols)[NG], float band_c, uint32_t bi, uint32_t jlo, uint32_t span, uint32_t n1,
                                          uint64_t total, const int32_t *__restrict__ c, const int32_t *__restrict__ r,
                                          uint32_t *__restrict__ bits, uint32_t lane)
 {
@@ -81,7 +83,7 @@ __device__ __forceinline__ void run_rows(const float4 (&cols)[NG], uint32_t bi, 
             bool hit;
             if (SMALL) {
                 bool near;
-                hit = collide_f32(pf, cols[g], near);
+                hit = collide_f32_banded(pf, cols[g], band_c, near);
                 redo = redo || near;
             } else {
                 const float4 q = cols[g];
@@ -136,25 +138,32 @@ __global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, ui
             const uint32_t jlo = bj * RHO, span = run * RHO;
             int4 q[NG];
             bool small = true;
+            uint32_t rm_c = 0, rm_r = 0;  // largest column and row radius of the run
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
                 const uint32_t j = jlo + 32 * g + lane;
                 q[g] = (32u * g < span + 32u && j < n1) ? sphere(c, r, j) : make_int4(0, 0, 0, 0);
                 small = small && small_coords(q[g]);
+                rm_c = max(rm_c, uint32_t(q[g].w));
             }
             const uint32_t rlast = min(bi * RHO + RHO, n1);  // the run's row spheres: bi rho + 1 .. rlast
-            for (uint32_t i = bi * RHO + 1 + lane; i <= rlast; i += 32) small = small && small_coords(sphere(c, r, i));
+            for (uint32_t i = bi * RHO + 1 + lane; i <= rlast; i += 32) {
+                const int4 pr = sphere(c, r, i);
+                small = small && small_coords(pr);
+                rm_r = max(rm_r, uint32_t(pr.w));
+            }
             float4 cols[NG];
             if (__all_sync(0xffffffffu, small)) {
+                const float rmax = float(__reduce_max_sync(0xffffffffu, rm_r) + __reduce_max_sync(0xffffffffu, rm_c));
 #pragma unroll
                 for (int g = 0; g < NG; ++g) cols[g] = as_float4(q[g]);
-                run_rows<RHO, true>(cols, bi, jlo, span, n1, total, c, r, bits, lane);
+                run_rows<RHO, true>(cols, 0x1p-20f * rmax * rmax, bi, jlo, span, n1, total, c, r, bits, lane);
             } else {
 #pragma unroll
                 for (int g = 0; g < NG; ++g)
                     cols[g] = make_float4(__int_as_float(q[g].x), __int_as_float(q[g].y), __int_as_float(q[g].z),
                                           __int_as_float(q[g].w));
-                run_rows<RHO, false>(cols, bi, jlo, span, n1, total, c, r, bits, lane);
+                run_rows<RHO, false>(cols, 0.0f, bi, jlo, span, n1, total, c, r, bits, lane);
             }
         }
     }

@@ -74,24 +74,27 @@ __device__ __forceinline__ bool collide_exact(const int4 &p, const int4 &q)
 }
 
 // The same predicate on the FP32 pipe, for coordinates in (-2^23, 2^23) (small_coords) carried
-// as floats: coordinate differences are then integers below 2^24 and exact in FP32, the sum of
-// squares s (one multiply, two FMAs) is within a factor (1 +- 3u) of the truth (u = 2^-24) and
-// R^2 (R exact) within (1 +- u).  Outside the relative band |s - R^2| <= 2^-20 R^2 the sign of
-// s - R^2 is therefore the exact answer; *band reports a pair inside it, which the caller must
-// decide again with collide_exact.
+// as floats: coordinate differences are then integers below 2^24 and exact in FP32, and the
+// radii sum R is exact.  s = fma(dx, dx, fma(dy, dy, dz dz)) is within 3u s_t of the exact sum
+// of squares s_t (u = 2^-24, first order), and diff = fma(-R, R, s) rounds s - R^2 once, so
+// with D = s_t - R^2 the error of diff is at most 3u R^2 + 4u |D|.  The sign of diff can differ
+// from that of D only if |D| <= 3.1u R^2, and then |diff| <= 6.2u R^2.  So with a band
+// band_c = 2^-20 Rmax^2 = 16u Rmax^2 for a group of pairs, Rmax >= R for every pair of the
+// group, |diff| > band_c proves the sign; *band reports a pair with |diff| <= band_c, which the
+// caller must decide again with collide_exact.
 __device__ __forceinline__ bool small_coords(const int4 &p)
 {
     const int32_t lim = 1 << 23;
     return p.x > -lim && p.x < lim && p.y > -lim && p.y < lim && p.z > -lim && p.z < lim;
 }
 
-__device__ __forceinline__ bool collide_f32(const float4 &p, const float4 &q, bool &band)
+__device__ __forceinline__ bool collide_f32_banded(const float4 &p, const float4 &q, float band_c, bool &band)
 {
     const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
     const float s = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float R = p.w + q.w, R2 = R * R;
-    const float diff = s - R2;
-    band = fabsf(diff) <= R2 * 0x1p-20f;
+    const float R = p.w + q.w;
+    const float diff = fmaf(-R, R, s);
+    band = fabsf(diff) <= band_c;
     return diff <= 0.0f;
 }
 

@@ -74,3 +74,22 @@ def test_collide_rejects():
         td.td_collide("UTM", "grid", c, r)
     with pytest.raises(td.TDError):
         td.td_collide("LTM", "chunked", c, r)
+
+
+def test_collide_many_exact_ties():
+    """Small integer cube and radii: s - R^2 is often exactly 0 or +-1, so most tiles take the FP32
+    band and the exact re-test (tiled table and block-mapped strict bits)."""
+    rng = np.random.default_rng(77)
+    for n in (100, 1000, 3000):
+        c = rng.integers(0, 16, (n, 3)).astype(np.int32)
+        r = rng.integers(0, 16, n).astype(np.int32)
+        s = ((c[:, None, :].astype(np.int64) - c[None, :, :]) ** 2).sum(-1)
+        R2 = (r[:, None].astype(np.int64) + r[None, :]) ** 2
+        assert np.count_nonzero(np.abs(s - R2) <= 1) > n // 8  # the case really is tie-heavy
+        ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+        got, _ = _table(c, r, "LTM", "persistent")
+        assert np.array_equal(got, oracle.collide(c, r)), n
+        words = td.td_collide_strict_words(n)
+        for rho in (8, 32):
+            bits, _ = td.td_collide_strict_blocks("LTM", ct, rt, rho)
+            assert np.array_equal(bits[:words].cpu().numpy().view(np.uint32), oracle.collide_strict(c, r)), (n, rho)
