@@ -25,7 +25,7 @@
 // integer test throughout.  The 32 row words stay in registers (a ballot result is the same in
 // every lane) and lane 0 writes the tile's 128 bytes; only diagonal and edge tiles apply the
 // validity mask (columns and rows below n, j < i on the diagonal).
-#include "td_device.cuh"
+#include "td_collide.cuh"
 #include "td_internal.h"
 #include "td_tiles.cuh"
 

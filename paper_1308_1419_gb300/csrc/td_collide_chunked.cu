@@ -24,6 +24,7 @@
 // with a pair inside the band is decided again with the integer test (spheres reloaded, off the
 // fast path);
 // otherwise the integer test decides every pair of the run.
+#include "td_collide.cuh"
 #include "td_internal.h"
 #include "td_tiles.cuh"
 

@@ -17,13 +17,14 @@
 //                            accumulators, each ring stage released by tcgen05.commit;
 //                  warps 2-17 epilogue: read the accumulator (warp w: TMEM lanes 32 (w mod 4) ..,
 //                            columns 32 ((w - 2) / 4) ..) and release it at once, form D^2, append
-//                            the cancelling pairs to a global queue (one atomic per warp and 32
-//                            columns), take the square root and write packed rows through a
-//                            per-warp transpose in shared memory.
+//                            the cancelling pairs to this CTA's segment of the queue (one
+//                            shared-memory atomic per warp and 32 columns), take the square root
+//                            and write packed rows through a per-warp transpose in shared memory.
 //                The two accumulators let the next block's loads and MMAs run under the epilogue.
 //   k_gram_fix   recomputes the queued pairs in the direct form: one warp per 2 pairs, 16-byte loads,
-//                lanes striding the features, partial sums combined in a fixed butterfly order.
-// If the queue is full, the epilogue recomputes the extra pairs itself.  Every mbarrier wait is
+//                lanes striding the features, partial sums combined in a fixed butterfly order; 32
+//                warps per queue segment.
+// If a segment is full, the epilogue recomputes the extra pairs itself.  Every mbarrier wait is
 // bounded; a timeout records an error code in the workspace status word and the roles wind down,
 // the tensor memory is released and the CTA ends.
 #include <cuda.h>
@@ -53,7 +54,7 @@ constexpr uint32_t SMEM_USED = OFF_BAR + 128;
 constexpr uint32_t SMEM_BYTES = SMEM_USED + 1024;  // slack for aligning the base
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
-// workspace status words (uint32): [0] error code, [1] reserved, [2..3] queued pairs (uint64)
+// workspace status words (uint32): [0] error code, [1] reserved, [2..3] recomputed pairs (uint64)
 enum : uint32_t { kErrNone = 0, kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3 };
 
 __device__ __forceinline__ float sqrt_approx(float v)
@@ -100,8 +101,8 @@ __device__ float direct_distance(const float *__restrict__ x, uint32_t d, uint32
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_gram(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ x, const float *__restrict__ norms,
-           uint32_t n, uint32_t d, uint32_t nt, float *__restrict__ out, uint2 *__restrict__ queue, uint64_t qcap,
-           uint32_t *__restrict__ status)
+           uint32_t n, uint32_t d, uint32_t nt, float *__restrict__ out, uint2 *__restrict__ queue, uint32_t seg,
+           uint32_t *__restrict__ seg_count, uint32_t *__restrict__ status)
 {
     using namespace sm100;
     extern __shared__ uint8_t smem_raw[];
@@ -116,6 +117,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 8 * (2 * STAGES + 4));
     volatile uint32_t *abort_flag = tmem_slot + 1;
     unsigned long long *qcount = reinterpret_cast<unsigned long long *>(status + 2);
+    uint32_t *scount = tmem_slot + 2;  // pairs this CTA has recomputed or queued (shared memory)
+    uint2 *qseg = queue + uint64_t(blockIdx.x) * seg;
 
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t nkb = (d + BK - 1) / BK;
@@ -132,6 +135,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         fence_mbar_init();
         *abort_flag = 0;
+        *scount = 0;
     }
     if (warp == 1) {
         tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
@@ -275,13 +279,13 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t total = __shfl_sync(0xffffffffu, pre, 31);
                 pre -= cnt;
                 unsigned long long slot0 = 0;
-                if (lane == 31) slot0 = atomicAdd(qcount, (unsigned long long)total);
+                if (lane == 31) slot0 = atomicAdd(scount, total);
                 slot0 = __shfl_sync(0xffffffffu, slot0, 31);
                 uint64_t slot = slot0 + pre;
                 for (uint32_t m = mask; m; m &= m - 1, ++slot) {
                     const uint32_t cc = __ffs(m) - 1, j = jb + cc;
-                    if (slot < qcap) queue[slot] = make_uint2(i, j);
-                    else st[lane * SLD + cc] = direct_distance(x, d, i, j);  // queue full: recompute here
+                    if (slot < seg) qseg[slot] = make_uint2(i, j);
+                    else st[lane * SLD + cc] = direct_distance(x, d, i, j);  // segment full: recompute here
                 }
             }
             __syncwarp();
@@ -308,30 +312,41 @@ __global__ void __launch_bounds__(THREADS, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
+    if (tid == 0) {
+        const uint32_t cnt = *scount;
+        seg_count[blockIdx.x] = cnt < seg ? cnt : seg;
+        if (cnt) atomicAdd(qcount, (unsigned long long)cnt);
+    }
 }
 
-// Direct FP32 recompute of the queued pairs: a warp takes FIX_PAIRS pairs at a time, lanes stride
-// the features 4 at a time (16-byte loads, two iterations in flight), and the per-lane partial
-// sums are combined in a fixed butterfly order.  d is a multiple of 4.
+// Direct FP32 recompute of the queued pairs: FIX_WARPS warps per queue segment, a warp takes
+// FIX_PAIRS pairs at a time, lanes stride the features 4 at a time (16-byte loads, two iterations
+// in flight), and the per-lane partial sums are combined in a fixed butterfly order.  d is a
+// multiple of 4.  Launched with gsize * FIX_WARPS / 8 CTAs of 256 threads.  (Walking all segments
+// as one list balances better but ran 1.7x slower on the clustered workload: every warp then
+// works in the same few blocks at once.)
 constexpr int FIX_PAIRS = 2;
+constexpr uint32_t FIX_WARPS = 32;
 
 __global__ void __launch_bounds__(256, 4) k_gram_fix(const float *__restrict__ x, uint32_t d,
                                                      const uint2 *__restrict__ queue,
-                                                     const uint32_t *__restrict__ status, uint64_t qcap,
-                                                     float *__restrict__ out)
+                                                     const uint32_t *__restrict__ seg_count, uint32_t seg,
+                                                     uint32_t gsize, float *__restrict__ out)
 {
-    const unsigned long long cnt = *reinterpret_cast<const unsigned long long *>(status + 2);
-    const uint64_t total = cnt < qcap ? cnt : qcap;
     const uint32_t lane = threadIdx.x & 31, d4 = d / 4;
-    const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-    for (uint64_t e = (uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * FIX_PAIRS; e < total;
-         e += warps * FIX_PAIRS) {
+    const uint32_t wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t c = wid % gsize, kw = wid / gsize;  // segment, and this warp's rank in it
+    if (kw >= FIX_WARPS) return;
+    const uint32_t cnt = seg_count[c];
+    const uint64_t total = cnt < seg ? cnt : seg;
+    const uint2 *qs = queue + uint64_t(c) * seg;
+    for (uint64_t e = uint64_t(kw) * FIX_PAIRS; e < total; e += FIX_WARPS * FIX_PAIRS) {
         const float4 *xi[FIX_PAIRS], *xj[FIX_PAIRS];
         uint2 pr[FIX_PAIRS];
         float part[FIX_PAIRS];
 #pragma unroll
         for (int p = 0; p < FIX_PAIRS; ++p) {
-            pr[p] = e + p < total ? queue[e + p] : make_uint2(0u, 0u);
+            pr[p] = e + p < total ? qs[e + p] : make_uint2(0u, 0u);
             xi[p] = reinterpret_cast<const float4 *>(x + uint64_t(pr[p].x) * d);
             xj[p] = reinterpret_cast<const float4 *>(x + uint64_t(pr[p].y) * d);
             part[p] = 0.0f;
@@ -381,11 +396,13 @@ EncodeTiledFn encode_fn()
 }
 
 struct GramLayout {
-    size_t norms, xb, queue, total;
-    uint64_t qcap;
+    size_t norms, xb, queue, counts, total;
+    uint32_t gsize, seg;
 };
 
-// status (256 B) | norms (n floats, zero-padded to whole blocks) | BF16 points | queue of cancelling pairs (qcap x 8 B)
+// status (256 B) | norms (n floats, zero-padded to whole blocks) | BF16 points | pair queue: one
+// segment of seg pairs (8 B) per k_gram CTA, T(n)/32 + 65536 pairs in all (twice the 1/64
+// fraction of clustered data, plus slack) | pairs queued per segment (uint32)
 GramLayout gram_layout(uint32_t n, uint32_t d)
 {
     GramLayout L;
@@ -393,8 +410,12 @@ GramLayout gram_layout(uint32_t n, uint32_t d)
     const size_t npad = size_t((n + BM - 1) / BM) * BM;
     L.xb = (L.norms + npad * 4 + 1023) & ~size_t(1023);
     L.queue = (L.xb + size_t(n) * d * 2 + 1023) & ~size_t(1023);
-    L.qcap = tri(n) / 32 + 65536;  // twice the 1/64 fraction of clustered data, plus slack
-    L.total = L.queue + L.qcap * 8;
+    const uint64_t tiles = tri((n + BM - 1) / BM), sms = uint64_t(sm_count());
+    L.gsize = static_cast<uint32_t>(tiles < sms ? (tiles ? tiles : 1) : sms);
+    const uint64_t seg = (tri(n) / 32 + 65536 + L.gsize - 1) / L.gsize;
+    L.seg = static_cast<uint32_t>(seg < 0xffffffffull ? seg : 0xffffffffull);
+    L.counts = (L.queue + size_t(L.gsize) * L.seg * 8 + 1023) & ~size_t(1023);
+    L.total = L.counts + size_t(L.gsize) * 4;
     return L;
 }
 
@@ -410,6 +431,7 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     auto *norms = reinterpret_cast<float *>(base + L.norms);
     auto *xb = reinterpret_cast<__nv_bfloat16 *>(base + L.xb);
     auto *queue = reinterpret_cast<uint2 *>(base + L.queue);
+    auto *seg_count = reinterpret_cast<uint32_t *>(base + L.counts);
     EncodeTiledFn enc = encode_fn();
     if (!enc) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     td_status s = cuda_status(cudaMemsetAsync(status, 0, 16, st), "td_edm_gram status reset");
@@ -430,13 +452,10 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     s = set_dynamic_smem_once(reinterpret_cast<const void *>(k_gram), SMEM_BYTES);
     if (s != TD_OK) return s;
     const uint32_t nt = (n + BM - 1) / BM;
-    const uint64_t tiles = tri(nt);
-    const uint64_t grid = tiles < uint64_t(sm_count()) ? tiles : uint64_t(sm_count());
-    k_gram<<<dim3(static_cast<uint32_t>(grid)), THREADS, SMEM_BYTES, st>>>(tmap, x, norms, n, d, nt, out, queue, L.qcap,
-                                                                          status);
+    k_gram<<<dim3(L.gsize), THREADS, SMEM_BYTES, st>>>(tmap, x, norms, n, d, nt, out, queue, L.seg, seg_count, status);
     s = launch_status("td_edm_gram kernel");
     if (s != TD_OK) return s;
-    k_gram_fix<<<dim3(4 * static_cast<uint32_t>(sm_count())), 256, 0, st>>>(x, d, queue, status, L.qcap, out);
+    k_gram_fix<<<dim3(L.gsize * (FIX_WARPS / 8)), 256, 0, st>>>(x, d, queue, seg_count, L.seg, L.gsize, out);
     return launch_status("td_edm_gram recompute kernel");
 }
 

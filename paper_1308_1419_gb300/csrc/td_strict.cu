@@ -12,7 +12,7 @@
 // The EDM sums in the order of every EDM kernel of libtd (t = x_i[k] - x_j[k], s = fma(t, t, s)
 // for k = 0 .. d-1 from s = 0, then sqrtf), so out[k] equals the with-diagonal map at (i, j) bit
 // for bit.
-#include "td_device.cuh"
+#include "td_collide.cuh"
 #include "td_internal.h"
 
 namespace td {
