@@ -199,17 +199,23 @@ struct EdmTile {
 #pragma unroll
                 for (int b = 0; b < TN; ++b) {
                     const float4 bv = features4<DELTA>(B, (tc + CT * b) * PLD + kk);
+                    float t[TM];  // one feature's differences for the TM rows first, then their FMAs
 #pragma unroll
-                    for (int a = 0; a < TM; ++a) {
-                        float t = av[a].x - bv.x;
-                        acc[a][b] = fmaf(t, t, acc[a][b]);
-                        t = av[a].y - bv.y;
-                        acc[a][b] = fmaf(t, t, acc[a][b]);
-                        t = av[a].z - bv.z;
-                        acc[a][b] = fmaf(t, t, acc[a][b]);
-                        t = av[a].w - bv.w;
-                        acc[a][b] = fmaf(t, t, acc[a][b]);
-                    }
+                    for (int a = 0; a < TM; ++a) t[a] = av[a].x - bv.x;
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) acc[a][b] = fmaf(t[a], t[a], acc[a][b]);
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) t[a] = av[a].y - bv.y;
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) acc[a][b] = fmaf(t[a], t[a], acc[a][b]);
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) t[a] = av[a].z - bv.z;
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) acc[a][b] = fmaf(t[a], t[a], acc[a][b]);
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) t[a] = av[a].w - bv.w;
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) acc[a][b] = fmaf(t[a], t[a], acc[a][b]);
                 }
             }
             __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
@@ -326,12 +332,13 @@ struct EdmTile {
                     }
                 } else {
 #pragma unroll
-                    for (int a = 0; a < TM; ++a)
+                    for (int a = 0; a < TM; ++a) {
+                        float t[TN];  // the row's differences first, then their FMAs
 #pragma unroll
-                        for (int b = 0; b < TN; ++b) {
-                            const float t = av[a] - bv[b];
-                            acc[a][b] = fmaf(t, t, acc[a][b]);
-                        }
+                        for (int b = 0; b < TN; ++b) t[b] = av[a] - bv[b];
+#pragma unroll
+                        for (int b = 0; b < TN; ++b) acc[a][b] = fmaf(t[b], t[b], acc[a][b]);
+                    }
                 }
             }
             __syncthreads();  // this buffer is refilled by the copies issued in the next iteration
