@@ -98,17 +98,20 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
 #pragma unroll
                 for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) xi[k] = (D || k < dd) ? __ldg(x + uint64_t(i + SHIFT) * dd + k) : 0.0f;
                 for (uint32_t jb = c0; jb < jhi; jb += 128) {
-#pragma unroll
-                    for (uint32_t m = 0; m < 4; ++m) {
-                        const uint32_t c = jb - jlo + lane + 32 * m;
-                        float s = 0.0f;
+                    {
+                        const uint32_t c = jb - jlo + lane;
+                        float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                         for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
                             if (D == 0 && k >= dd) break;
-                            const float t = xi[k] - sx[k * sl + c];
-                            s = fmaf(t, t, s);
+                            float t[4];
+#pragma unroll
+                            for (uint32_t m = 0; m < 4; ++m) t[m] = xi[k] - sx[k * sl + c + 32 * m];
+#pragma unroll
+                            for (uint32_t m = 0; m < 4; ++m) s[m] = fmaf(t[m], t[m], s[m]);
                         }
-                        sres[lane + 32 * m] = sqrtf(s);
+#pragma unroll
+                        for (uint32_t m = 0; m < 4; ++m) sres[lane + 32 * m] = sqrtf(s[m]);
                     }
                     __syncwarp();
                     const uint32_t j = jb + 4 * lane;
