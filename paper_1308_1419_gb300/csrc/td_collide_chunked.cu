@@ -10,20 +10,19 @@
 // T(i1) + [jlo, jhi), jlo = bj rho, jhi = min((bj + run) rho, i1 + 1), and each 32-bit word of
 // the array is decided by the run holding its first bit.
 //
-// Per run, lane l holds the column spheres jlo + 32 g + l, g < NG, in registers (the run's
-// columns and the 32 after them).  Per element row the row sphere is a broadcast load, and
-// group g's 32 predicates become one ballot b_g over columns jlo + 32 g ...; with
-// a = (T(i1) + jlo) mod 32 the bit of column jlo + 32 g + l sits at bit (a + l) mod 32 of word
-// (T(i1) + jlo) / 32 + g (+1 when a + l >= 32), so that word is the funnel shift of b_(g-1)
-// and b_g by a.  Lane g keeps word g and the row's words leave in one store.  The one word per
-// row that runs past the end of row i1 into the next row(s) is decided lane by lane from global
-// memory.
+// Per run, the warp stages the run's column spheres (and the 32 after them) as float4s in its
+// slice of shared memory, and the run's row spheres.  For element row i1 the first owned word
+// starts at column q0 of the run, (T(i1) + jlo + q0) a multiple of 32, so lane l reading column
+// q0 + 32 g + l makes the ballot of group g word g of the row itself: no shifting, one 16-byte
+// shared load per pair, conflict-free.  The row's up to 8 words are decided in a loop without an
+// exit (unused groups are computed and dropped) and written by lane 0.  The one word per row that
+// runs past the end of row i1 into the next row(s) is decided lane by lane from global memory.
 //
 // The predicate is collide_exact's.  When every coordinate of the run's spheres is below 2^23
 // in magnitude it is taken on the FP32 pipe (collide_f32_banded, one band for the run), and a row
 // with a pair inside the band is decided again with the integer test (spheres reloaded, off the
-// fast path);
-// otherwise the integer test decides every pair of the run.
+// fast path); otherwise the integer test decides every pair of the run (the staged values are
+// then the integers, bit for bit).
 #include "td_collide.cuh"
 #include "td_internal.h"
 #include "td_tiles.cuh"
@@ -32,7 +31,8 @@ namespace td {
 namespace {
 
 constexpr uint32_t kWarps = 8, kStrip = 256;
-constexpr int NG = kStrip / 32 + 1;  // column groups a lane holds: the widest run and 32 more columns
+constexpr uint32_t kCols = kStrip + 32;  // staged columns per run: the widest run and 32 more
+constexpr int NW = kStrip / 32;          // words per row and run, at most
 
 __device__ __forceinline__ int4 sphere(const int32_t *__restrict__ c, const int32_t *__restrict__ r, uint32_t j)
 {
@@ -41,6 +41,14 @@ __device__ __forceinline__ int4 sphere(const int32_t *__restrict__ c, const int3
 }
 
 __device__ __forceinline__ float4 as_float4(const int4 &p) { return make_float4(float(p.x), float(p.y), float(p.z), float(p.w)); }
+__device__ __forceinline__ float4 bits_float4(const int4 &p)
+{
+    return make_float4(__int_as_float(p.x), __int_as_float(p.y), __int_as_float(p.z), __int_as_float(p.w));
+}
+__device__ __forceinline__ int4 bits_int4(const float4 &p)
+{
+    return make_int4(__float_as_int(p.x), __float_as_int(p.y), __float_as_int(p.z), __float_as_int(p.w));
+}
 
 // The crossing word at position P (a multiple of 32, P < total): lane l decides bit P + l.
 __device__ __forceinline__ bool crossing_bit(const int32_t *__restrict__ c, const int32_t *__restrict__ r, uint64_t P,
@@ -57,63 +65,57 @@ __device__ __forceinline__ bool crossing_bit(const int32_t *__restrict__ c, cons
     return collide_exact(sphere(c, r, ii + 1), sphere(c, r, static_cast<uint32_t>(Pl - tii)));
 }
 
-// One run's element rows.  SMALL: cols hold the column spheres as floats (every coordinate of
-// the run below 2^23) and band_c is the run's FP32 band (collide_f32_banded), else cols hold the
-// integers (reinterpreted).  Every row decides all NG groups (the
-// groups past the row's last word are not stored): a loop without an exit lets the groups'
-// independent predicate chains overlap.
+// One run's element rows from the staged spheres.  SMALL: staged as floats, decided on the FP32
+// pipe with band band_c; else staged as the integers and decided exactly.
 template <int RHO, bool SMALL>
-__device__ __forceinline__ void run_rows(const float4 (&cols)[NG], float band_c, uint32_t bi, uint32_t jlo, uint32_t span, uint32_t n1,
-                                         uint64_t total, const int32_t *__restrict__ c, const int32_t *__restrict__ r,
-                                         uint32_t *__restrict__ bits, uint32_t lane)
+__device__ __forceinline__ void run_rows(const float4 *cols, const float4 *rows, float band_c, uint32_t bi, uint32_t jlo,
+                                         uint32_t span, uint32_t n1, uint64_t total, const int32_t *__restrict__ c,
+                                         const int32_t *__restrict__ r, uint32_t *__restrict__ bits, uint32_t lane)
 {
-    const uint32_t rend = min(bi * RHO + RHO, n1);  // element rows bi rho .. rend - 1
-    int4 pn = sphere(c, r, bi * RHO + 1);
-    for (uint32_t i1 = bi * RHO; i1 < rend; ++i1) {  // element row: pairs (i1 + 1, j), j <= i1
-        const int4 p = pn;
-        if (i1 + 1 < rend) pn = sphere(c, r, i1 + 2);  // the next row's sphere, loaded under this row
-        const float4 pf = as_float4(p);
+    for (uint32_t rr = 0; rr < uint32_t(RHO); ++rr) {
+        const uint32_t i1 = bi * RHO + rr;  // element row: pairs (i1 + 1, j), j <= i1
+        if (i1 >= n1) break;
         const uint64_t ti = tri(i1);
         const uint32_t L = min(jlo + span, i1 + 1) - jlo;  // columns of the row in this run
-        const uint32_t a = static_cast<uint32_t>(ti + jlo) & 31u;
-        const uint64_t w0 = (ti + jlo) >> 5;
-        uint32_t prev = 0, mine = 0;
+        const uint64_t P0 = (ti + jlo + 31) & ~uint64_t(31);   // the first owned word
+        const uint32_t q0 = static_cast<uint32_t>(P0 - ti - jlo);
+        if (q0 >= L) continue;                                 // no word starts in this row and run
+        const uint32_t nw = (L - q0 + 31) / 32;                // words starting in the run
+        const bool cross = q0 + 32 * (nw - 1) + 31 > i1 - jlo; // the last one runs past the row end
+        const uint32_t nfull = cross ? nw - 1 : nw;
+        const float4 p = rows[rr];
+        uint32_t w[NW];
         bool redo = false;
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
+        for (int g = 0; g < NW; ++g) {
+            const float4 q4 = cols[q0 + 32 * g + lane];
             bool hit;
             if (SMALL) {
                 bool near;
-                hit = collide_f32_banded(pf, cols[g], band_c, near);
-                redo = redo || near;
+                hit = collide_f32_banded(p, q4, band_c, near);
+                redo = redo || (near && uint32_t(g) < nfull);
             } else {
-                const float4 q = cols[g];
-                hit = collide_exact(p, make_int4(__float_as_int(q.x), __float_as_int(q.y), __float_as_int(q.z),
-                                                 __float_as_int(q.w)));
+                hit = collide_exact(bits_int4(p), bits_int4(q4));
             }
-            const uint32_t b = __ballot_sync(0xffffffffu, hit);
-            if (lane == uint32_t(g)) mine = __funnelshift_l(prev, b, a);  // word g: columns jlo + 32 g - a ..
-            prev = b;
+            w[g] = __ballot_sync(0xffffffffu, hit);
         }
-        // words g_first = (a ? 1 : 0) .. g_last = (L - 1 + a) / 32 start inside the run; the last
-        // one may run past the end of row i1
-        const uint32_t g_first = a ? 1u : 0u, g_last = (L - 1 + a) >> 5;
-        if (SMALL && __any_sync(0xffffffffu, redo)) {  // a pair in the FP32 band: the row again, exactly
-            prev = 0;
-            for (uint32_t g = 0; g <= g_last; ++g) {
-                const uint32_t j = jlo + 32 * g + lane;  // columns past i1 feed no whole word
-                const uint32_t b = __ballot_sync(0xffffffffu, j <= i1 && collide_exact(p, sphere(c, r, j)));
-                if (lane == g) mine = __funnelshift_l(prev, b, a);
-                prev = b;
-            }
+        if (SMALL && __any_sync(0xffffffffu, redo)) {  // a pair in the FP32 band: the row's words again, exactly
+            const int4 pe = sphere(c, r, i1 + 1);
+#pragma unroll
+            for (int g = 0; g < NW; ++g)
+                if (uint32_t(g) < nfull)
+                    w[g] = __ballot_sync(0xffffffffu, collide_exact(pe, sphere(c, r, jlo + q0 + 32 * g + lane)));
         }
-        const bool cross = g_last >= g_first && 32u * g_last + 31u - a > i1 - jlo;
-        const uint32_t g_full = cross ? g_last : g_last + 1;  // the words before it are whole
-        if (lane >= g_first && lane < g_full) bits[w0 + lane] = mine;
+        uint32_t *wrow = bits + (P0 >> 5);
+        if (lane == 0) {
+#pragma unroll
+            for (int g = 0; g < NW; ++g)
+                if (uint32_t(g) < nfull) wrow[g] = w[g];
+        }
         if (cross) {
-            const uint64_t P = (w0 + g_last) << 5;
-            const uint32_t word = __ballot_sync(0xffffffffu, crossing_bit(c, r, P, i1, ti, total, lane));
-            if (lane == 0) bits[w0 + g_last] = word;
+            const uint32_t word =
+                __ballot_sync(0xffffffffu, crossing_bit(c, r, P0 + 32 * uint64_t(nw - 1), i1, ti, total, lane));
+            if (lane == 0) wrow[nw - 1] = word;
         }
     }
 }
@@ -124,7 +126,10 @@ __global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, ui
                                                                  const int32_t *__restrict__ r,
                                                                  uint32_t *__restrict__ bits)
 {
+    __shared__ __align__(16) float4 scol[kWarps][kCols];
+    __shared__ __align__(16) float4 srow[kWarps][32];
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4 *cols = scol[warp], *rows = srow[warp];
     const uint64_t total = tri(n1);
     const uint64_t warps = uint64_t(gridDim.x) * kWarps;
     const uint64_t strips = (tiles.units + S - 1) / S;
@@ -137,35 +142,39 @@ __global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, ui
             u += run;
             if (!ok) continue;
             const uint32_t jlo = bj * RHO, span = run * RHO;
-            int4 q[NG];
+            __syncwarp();  // the previous run's reads of the slice are done
             bool small = true;
-            uint32_t rm_c = 0, rm_r = 0;  // largest column and row radius of the run
+            uint32_t rm = 0;  // largest radius staged
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
-                const uint32_t j = jlo + 32 * g + lane;
-                q[g] = (32u * g < span + 32u && j < n1) ? sphere(c, r, j) : make_int4(0, 0, 0, 0);
-                small = small && small_coords(q[g]);
-                rm_c = max(rm_c, uint32_t(q[g].w));
+            for (uint32_t k = 0; k < kCols / 32; ++k) {
+                const uint32_t q = lane + 32 * k, j = jlo + q;
+                const int4 s4 = (q < span + 32 && j < n1) ? sphere(c, r, j) : make_int4(0, 0, 0, 0);
+                small = small && small_coords(s4);
+                rm = max(rm, uint32_t(s4.w));
+                cols[q] = as_float4(s4);
             }
-            const uint32_t rlast = min(bi * RHO + RHO, n1);  // the run's row spheres: bi rho + 1 .. rlast
-            for (uint32_t i = bi * RHO + 1 + lane; i <= rlast; i += 32) {
-                const int4 pr = sphere(c, r, i);
-                small = small && small_coords(pr);
-                rm_r = max(rm_r, uint32_t(pr.w));
+            uint32_t rmr = 0;
+            {
+                const uint32_t i1 = bi * RHO + lane;  // lane q < rho stages row sphere bi rho + q + 1
+                const int4 p4 = (lane < uint32_t(RHO) && i1 < n1) ? sphere(c, r, i1 + 1) : make_int4(0, 0, 0, 0);
+                small = small && small_coords(p4);
+                rmr = uint32_t(p4.w);
+                rows[lane] = as_float4(p4);
             }
-            float4 cols[NG];
-            if (__all_sync(0xffffffffu, small)) {
-                const float rmax = float(__reduce_max_sync(0xffffffffu, rm_r) + __reduce_max_sync(0xffffffffu, rm_c));
+            const bool all_small = __all_sync(0xffffffffu, small);
+            if (!all_small) {  // large coordinates: the integers themselves, bit for bit
 #pragma unroll
-                for (int g = 0; g < NG; ++g) cols[g] = as_float4(q[g]);
-                run_rows<RHO, true>(cols, 0x1p-20f * rmax * rmax, bi, jlo, span, n1, total, c, r, bits, lane);
-            } else {
-#pragma unroll
-                for (int g = 0; g < NG; ++g)
-                    cols[g] = make_float4(__int_as_float(q[g].x), __int_as_float(q[g].y), __int_as_float(q[g].z),
-                                          __int_as_float(q[g].w));
-                run_rows<RHO, false>(cols, 0.0f, bi, jlo, span, n1, total, c, r, bits, lane);
+                for (uint32_t k = 0; k < kCols / 32; ++k) {
+                    const uint32_t q = lane + 32 * k, j = jlo + q;
+                    cols[q] = bits_float4((q < span + 32 && j < n1) ? sphere(c, r, j) : make_int4(0, 0, 0, 0));
+                }
+                const uint32_t i1 = bi * RHO + lane;
+                rows[lane] = bits_float4((lane < uint32_t(RHO) && i1 < n1) ? sphere(c, r, i1 + 1) : make_int4(0, 0, 0, 0));
             }
+            const float rmax = float(__reduce_max_sync(0xffffffffu, rm) + __reduce_max_sync(0xffffffffu, rmr));
+            __syncwarp();
+            if (all_small) run_rows<RHO, true>(cols, rows, 0x1p-20f * rmax * rmax, bi, jlo, span, n1, total, c, r, bits, lane);
+            else run_rows<RHO, false>(cols, rows, 0.0f, bi, jlo, span, n1, total, c, r, bits, lane);
         }
     }
 }
