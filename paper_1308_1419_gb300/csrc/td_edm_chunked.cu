@@ -8,7 +8,8 @@
 // its rho element rows i, the contiguous packed range T(i) + [bj rho, min((bj + run) rho, i + 1)),
 // and an aligned 16-byte chunk of the packed output is written by the run holding its first
 // element.  Per run, the warp stages the column points x_j, j = bj rho .. bj rho + run rho + 3,
-// feature-major in its slice of shared memory.  Per element row it keeps x_i in registers and
+// in its slice of shared memory: one float4 per point for d = 3 and 4 (one 16-byte load per
+// pair), feature-major rows otherwise.  Per element row it keeps x_i in registers and
 // computes 128 columns at a time, lane l taking columns c + l + 32 m (m < 4: conflict-free shared
 // reads); the 128 results go through a per-warp buffer so that lane l then stores the aligned
 // chunk c + 4l .. c + 4l + 3 with one 16-byte streaming store.  A chunk that runs past the end of
@@ -32,11 +33,18 @@ namespace {
 constexpr uint32_t kWarps = 8, kMaxD = 8;
 constexpr uint32_t kPad = 132;  // staged floats per feature row beyond the strip width (multiple of 4)
 
-// Widest strip a warp's shared-memory slice holds: (d sl + 128) floats per warp, sl = W + kPad.
-// Beyond d = 3 the slices of 512-element strips cost more occupancy than the longer runs gain
-// (n = 32768, d = 4: 0.83 ms at 512, 0.73 ms at 256).
-constexpr uint32_t edm_chunk_wmax(uint32_t d) { return d <= 3 ? 512u : 256u; }
-constexpr size_t edm_chunk_smem(uint32_t d, uint32_t w) { return size_t(kWarps) * (d * (w + kPad) + 128) * 4; }
+// d = 3 and 4 stage each column point as one float4 (one 16-byte shared load per pair); other d
+// stage d feature rows.  Floats staged per column:
+constexpr bool edm_chunk_pm(uint32_t d) { return d == 3 || d == 4; }
+constexpr uint32_t edm_chunk_fpc(uint32_t d) { return edm_chunk_pm(d) ? 4u : d; }
+// Widest strip a warp's shared-memory slice holds: (fpc sl + 128) floats per warp, sl = W + kPad.
+// With more than 2 floats per column the slices of 512-element strips cost more occupancy than
+// the longer runs gain (n = 32768, d = 4: 0.83 ms at 512, 0.73 ms at 256).
+constexpr uint32_t edm_chunk_wmax(uint32_t d) { return edm_chunk_fpc(d) <= 2 ? 512u : 256u; }
+constexpr size_t edm_chunk_smem(uint32_t d, uint32_t w)
+{
+    return size_t(kWarps) * (edm_chunk_fpc(d) * (w + kPad) + 128) * 4;
+}
 
 template <int D>
 __device__ __forceinline__ float direct(const float *__restrict__ x, uint32_t d, uint32_t i, uint32_t j)
@@ -61,10 +69,12 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
                                                              float *__restrict__ out)
 {
     extern __shared__ __align__(16) float esm[];
-    const uint32_t dd = D ? D : d;
+    constexpr bool PM = edm_chunk_pm(D);  // column c staged as the float4 sx4[c] (d = 3, 4)
+    const uint32_t dd = D ? D : d, fpc = PM ? 4u : dd;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float *sx = esm + warp * (dd * sl + 128);  // dd feature rows of sl floats: column c of the run
-    float *sres = sx + dd * sl;                // results of the current 128 columns
+    float *sx = esm + warp * (fpc * sl + 128);  // dd feature rows of sl floats: column c of the run
+    float4 *sx4 = reinterpret_cast<float4 *>(sx);
+    float *sres = sx + fpc * sl;                // results of the current 128 columns
     const uint64_t warps = uint64_t(gridDim.x) * kWarps;
     const uint64_t strips = (tiles.units + S - 1) / S;
     for (uint64_t z = uint64_t(blockIdx.x) * kWarps + warp; z < strips; z += warps) {
@@ -80,10 +90,21 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
             for (uint32_t c = lane; c < ncol; c += 32) {
                 const uint32_t j = jlo + c;
                 const float *xj = x + uint64_t(j) * dd;
+                if (PM) {
+                    float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (j < n) {
+                        v.x = __ldg(xj);
+                        v.y = __ldg(xj + 1);
+                        v.z = __ldg(xj + 2);
+                        if (D == 4) v.w = __ldg(xj + 3);
+                    }
+                    sx4[c] = v;
+                } else {
 #pragma unroll
-                for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
-                    if (D == 0 && k >= dd) break;
-                    sx[k * sl + c] = j < n ? __ldg(xj + k) : 0.0f;
+                    for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
+                        if (D == 0 && k >= dd) break;
+                        sx[k * sl + c] = j < n ? __ldg(xj + k) : 0.0f;
+                    }
                 }
             }
             __syncwarp();
@@ -101,14 +122,30 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
                     {
                         const uint32_t c = jb - jlo + lane;
                         float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                        if (PM) {
+                            float4 q[4];
 #pragma unroll
-                        for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
-                            if (D == 0 && k >= dd) break;
-                            float t[4];
+                            for (uint32_t m = 0; m < 4; ++m) q[m] = sx4[c + 32 * m];
+                            const float qv[4][4] = {{q[0].x, q[0].y, q[0].z, q[0].w}, {q[1].x, q[1].y, q[1].z, q[1].w},
+                                                    {q[2].x, q[2].y, q[2].z, q[2].w}, {q[3].x, q[3].y, q[3].z, q[3].w}};
 #pragma unroll
-                            for (uint32_t m = 0; m < 4; ++m) t[m] = xi[k] - sx[k * sl + c + 32 * m];
+                            for (uint32_t k = 0; k < uint32_t(D); ++k) {
+                                float t[4];
 #pragma unroll
-                            for (uint32_t m = 0; m < 4; ++m) s[m] = fmaf(t[m], t[m], s[m]);
+                                for (uint32_t m = 0; m < 4; ++m) t[m] = xi[k] - qv[m][k];
+#pragma unroll
+                                for (uint32_t m = 0; m < 4; ++m) s[m] = fmaf(t[m], t[m], s[m]);
+                            }
+                        } else {
+#pragma unroll
+                            for (uint32_t k = 0; k < (D ? D : kMaxD); ++k) {
+                                if (D == 0 && k >= dd) break;
+                                float t[4];
+#pragma unroll
+                                for (uint32_t m = 0; m < 4; ++m) t[m] = xi[k] - sx[k * sl + c + 32 * m];
+#pragma unroll
+                                for (uint32_t m = 0; m < 4; ++m) s[m] = fmaf(t[m], t[m], s[m]);
+                            }
                         }
 #pragma unroll
                         for (uint32_t m = 0; m < 4; ++m) sres[lane + 32 * m] = sqrtf(s[m]);
