@@ -121,7 +121,7 @@ __device__ __forceinline__ void run_rows(const float4 *cols, const float4 *rows,
 }
 
 template <class Tiles, int RHO>
-__global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, uint32_t n1, uint32_t S,
+__global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, uint32_t n1, uint32_t S, uint32_t rcap,
                                                                  const int32_t *__restrict__ c,
                                                                  const int32_t *__restrict__ r,
                                                                  uint32_t *__restrict__ bits)
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, ui
         for (uint64_t u = z * S; u < uend;) {
             uint32_t bi, bj;
             const bool ok = tiles(u, bi, bj);
-            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(uend - u));
+            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(min(uend - u, uint64_t(rcap))));
             u += run;
             if (!ok) continue;
             const uint32_t jlo = bj * RHO, span = run * RHO;
@@ -186,12 +186,12 @@ td_status launch_tiles(const Tiles &t, const int32_t *c, const int32_t *r, uint3
     if (t.units == 0) return TD_OK;
     auto k = k_collide_chunked<Tiles, RHO>;
     const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, ~0ull) * kWarps;
-    const uint32_t w = chunked_strip_width(t.units, RHO, resident, kStrip, kStrip);
-    if (w > kStrip || w < uint32_t(RHO)) return fail(TD_ERR_INVALID_ARG, "strict collision strip width %u", w);
-    const uint32_t S = w / RHO;
+    const ChunkPlan cp = chunked_plan(t.units, RHO, resident, kStrip, kStrip);
+    if (cp.W > kStrip || cp.W < uint32_t(RHO)) return fail(TD_ERR_INVALID_ARG, "strict collision run width %u", cp.W);
+    const uint32_t S = cp.S;
     const uint64_t strips = (t.units + S - 1) / S;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, (strips + kWarps - 1) / kWarps);
-    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, 0, st>>>(t, n1, S, c, r, bits);
+    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, 0, st>>>(t, n1, S, cp.rcap, c, r, bits);
     *ctas += g;
     return launch_status("td_collide_strict_blocks kernel");
 }

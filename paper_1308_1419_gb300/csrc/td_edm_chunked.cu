@@ -3,8 +3,8 @@
 // features the map is store-bound, and one element per thread (td_edm_pair.cu) leaves the HBM
 // write rate far behind; this body stores aligned 16-byte chunks instead.
 //
-// Warps walk strips of S = W / rho consecutive units as the chunked probe does (td_probe.cu): a
-// run of consecutive blocks (bi, bj) .. (bi, bj + run - 1) of one block row covers, in each of
+// Warps walk strips of consecutive units as the chunked probe does (td_probe.cu): a run of at most
+// W / rho consecutive blocks (bi, bj) .. (bi, bj + run - 1) of one block row covers, in each of
 // its rho element rows i, the contiguous packed range T(i) + [bj rho, min((bj + run) rho, i + 1)),
 // and an aligned 16-byte chunk of the packed output is written by the run holding its first
 // element.  Per run, the warp stages the column points x_j, j = bj rho .. bj rho + run rho + 3,
@@ -64,7 +64,7 @@ __device__ __forceinline__ float direct(const float *__restrict__ x, uint32_t d,
 // n: side of the packed triangle (the number of points minus SHIFT); row i of it pairs point
 // i + SHIFT with the points j <= i.
 template <class Tiles, int RHO, int D, int SHIFT>
-__global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uint32_t n, uint32_t S, uint32_t sl,
+__global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uint32_t n, uint32_t S, uint32_t rcap, uint32_t sl,
                                                              const float *__restrict__ x, uint32_t d,
                                                              float *__restrict__ out)
 {
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
         for (uint64_t u = z * S; u < uend;) {
             uint32_t bi, bj;
             const bool ok = tiles(u, bi, bj);
-            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(uend - u));
+            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(min(uend - u, uint64_t(rcap))));
             u += run;
             if (!ok) continue;
             const uint32_t jlo = bj * RHO, ncol = run * RHO + 4;
@@ -187,12 +187,12 @@ td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, f
     td_status s = set_dynamic_smem_once(reinterpret_cast<const void *>(k), smax);
     if (s != TD_OK) return s;
     const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smax, ~0ull) * kWarps;
-    const uint32_t w = chunked_strip_width(t.units, RHO, resident, wmax, wmax);
-    const uint32_t S = w / RHO, sl = w + kPad;
-    const size_t smem = edm_chunk_smem(d, w);
-    const uint64_t strips = (t.units + S - 1) / S;
+    const ChunkPlan cp = chunked_plan(t.units, RHO, resident, wmax, wmax);
+    const uint32_t sl = cp.W + kPad;
+    const size_t smem = edm_chunk_smem(d, cp.W);
+    const uint64_t strips = (t.units + cp.S - 1) / cp.S;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smem, (strips + kWarps - 1) / kWarps);
-    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, smem, st>>>(t, n, S, sl, x, d, out);
+    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, smem, st>>>(t, n, cp.S, cp.rcap, sl, x, d, out);
     *ctas += g;
     return launch_status("td_edm chunked kernel");
 }

@@ -36,11 +36,16 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
 // Launchers (stream-ordered, no synchronisation).
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
                        bool cover, const Plan &p, cudaStream_t st, uint64_t *ctas);
-// Strip width (elements of one packed row) of the chunked schedule: the widest power of two in
-// [min(256, wauto), wauto] leaving at least four strips per resident warp; below that (down to
-// rho, one block per strip) while there are fewer strips than resident warps; or the
-// TD_OPT_PROBE_STRIP value (capped at wlimit).  Never below rho.
-uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit);
+// Shape of a chunked launch.  W: the widest run (consecutive blocks of one block row), in elements
+// of one packed row: the widest power of two in [min(256, wauto), wauto] leaving at least four
+// runs of W per resident warp, or the TD_OPT_PROBE_STRIP value (capped at wlimit); never below rho.
+// rcap = W / rho units.  S: units per strip (one warp's contiguous share): rcap while there are at
+// least four strips per resident warp, else the launch split evenly, ceil(units / warps) -- with
+// only a few strips per warp, whole strips would leave most warps idle for the last round.
+struct ChunkPlan {
+    uint32_t W, rcap, S;
+};
+ChunkPlan chunked_plan(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit);
 td_status launch_edm_strict(const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st);
 td_status launch_collide_strict(const int32_t *c, const int32_t *r, uint32_t n, uint32_t *bits, cudaStream_t st);
 // strict: the strict lower triangle of the n points, as the packed triangle of side n - 1 whose

@@ -38,11 +38,11 @@ struct CoverBody {
 };
 
 // ---------------------------------------------------------------- chunked probe (block strategies)
-// Persistent warps walk the launch space in strips of S = W / rho consecutive units (W, the strip
-// width in elements, a power of two >= 128 chosen per launch).  Units
-// that continue one block row -- blocks (bi, bj), (bi, bj+1), ... -- cover, in each element row
-// i of that block row, one contiguous flat range [s, e) of the packed output (s = T(i) + bj rho),
-// at most W elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
+// Persistent warps walk the launch space in strips of S consecutive units (chunked_plan: W / rho
+// for large launches, W a power of two chosen per launch, or an even share per warp for small
+// ones).  Units that continue one block row -- blocks (bi, bj), (bi, bj+1), ..., at most W / rho
+// of them -- cover, in each element row i of that block row, one contiguous flat range [s, e) of
+// the packed output (s = T(i) + bj rho), at most W elements long.  The flat output is cut into aligned 4-element (16-byte) chunks,
 // and chunk c is written by the block row range holding its first element 4c: the blocks of
 // every block strategy cover each element exactly once, so each chunk has exactly one writer.
 // All 32 lanes of a warp work on the same element row, lane l on chunks l, l + 32, ... of [s, e),
@@ -93,7 +93,8 @@ __device__ __forceinline__ void probe_chunk(uint32_t *__restrict__ out, uint32_t
 // CPL > 0: strips at most 128 CPL elements wide, each lane's chunks of a row in a fully unrolled
 // loop; CPL = 0: any width, a runtime loop (the wide strips of large launches).
 template <class Tiles, int RHO, int CPL>
-__global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t S, uint32_t *__restrict__ out)
+__global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t S, uint32_t rcap,
+                                                     uint32_t *__restrict__ out)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
         for (uint64_t u = z * S; u < uend;) {
             uint32_t bi, bj;
             const bool ok = tiles(u, bi, bj);
-            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(uend - u));
+            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(min(uend - u, uint64_t(rcap))));
             u += run;
             if (!ok) continue;
             const uint32_t jlo = bj * RHO;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
 // Strip width: longer contiguous row segments per warp raise the write bandwidth at large N
 // (more of each DRAM page is written by one warp), but fewer strips balance worse over the
 // resident warps.  Default: the widest power of two in [256, kStripMax] that still leaves four
-// strips per resident warp (chunked_strip_width); the library option overrides it.
+// strips per resident warp (chunked_plan); the library option overrides it.
 constexpr uint32_t kStripMax = 2048;
 
 
@@ -144,11 +145,11 @@ td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaSt
     auto wide = k_probe_chunked<Tiles, RHO, 0>;
     auto narrow = k_probe_chunked<Tiles, RHO, 2>;
     const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(wide), 256, 0, ~0ull) * 8;
-    const uint32_t W = chunked_strip_width(t.units, RHO, resident, kStripMax, 8192), S = W / RHO;
-    const auto k = W <= 256 ? narrow : wide;
-    const uint64_t strips = (t.units + S - 1) / S;
+    const ChunkPlan cp = chunked_plan(t.units, RHO, resident, kStripMax, 8192);
+    const auto k = cp.W <= 256 ? narrow : wide;
+    const uint64_t strips = (t.units + cp.S - 1) / cp.S;
     const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 256, 0, (strips + 7) / 8);
-    k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, S, out);
+    k<<<dim3(static_cast<uint32_t>(g)), 256, 0, st>>>(t, N, cp.S, cp.rcap, out);
     *ctas += g;
     return launch_status("td probe chunked kernel");
 }
@@ -264,7 +265,7 @@ td_status launch_variant(td_mapping m, bool P, uint32_t N, uint32_t rho, Body bo
 
 }  // namespace
 
-uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit)
+ChunkPlan chunked_plan(uint64_t units, uint32_t rho, uint64_t resident_warps, uint32_t wauto, uint32_t wlimit)
 {
     const int forced = option(TD_OPT_PROBE_STRIP);
     uint32_t w = wauto < 256 ? wauto : 256;
@@ -272,11 +273,18 @@ uint32_t chunked_strip_width(uint64_t units, uint32_t rho, uint64_t resident_war
         w = uint32_t(forced) < wlimit ? uint32_t(forced) : wlimit;
     } else {
         while (w < wauto && units * rho / (2 * w) >= 4 * resident_warps) w *= 2;
-        // small launch: rather one block per strip than fewer strips than resident warps (a
-        // warp walking a long strip alone on its SM exposes every instruction's latency)
-        while (w > rho && units * rho / w < resident_warps) w /= 2;
     }
-    return w < rho ? rho : w;
+    ChunkPlan p;
+    p.W = w < rho ? rho : w;
+    p.rcap = p.W / rho;
+    if (resident_warps == 0) resident_warps = 1;
+    if (units >= 4 * resident_warps * p.rcap) {
+        p.S = p.rcap;
+    } else {
+        const uint64_t share = (units + resident_warps - 1) / resident_warps;
+        p.S = static_cast<uint32_t>(share ? share : 1);
+    }
+    return p;
 }
 
 td_status launch_dummy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *sink, const Plan &p,
