@@ -13,8 +13,8 @@
 // computes 128 columns at a time, lane l taking columns c + l + 32 m (m < 4: conflict-free shared
 // reads); the 128 results go through a per-warp buffer so that lane l then stores the aligned
 // chunk c + 4l .. c + 4l + 3 with one 16-byte streaming store.  A chunk that runs past the end of
-// row i into the next row(s) is computed element by element from global memory (at most one
-// chunk per row).
+// row i into the next row(s) (at most one per row) is computed from global memory after the run's
+// rows, lane r taking row r, so the rows' crossings share their memory latency.
 //
 // The same kernel serves the strict lower triangle (td-problems without the diagonal, Eq.
 // (theorem_nodiag) of Sec. II-A): its pairs (i, j), j < i < n, packed at i(i-1)/2 + j, form the
@@ -59,6 +59,53 @@ __device__ __forceinline__ float direct(const float *__restrict__ x, uint32_t d,
         s = fmaf(t, t, s);
     }
     return sqrtf(s);
+}
+
+// The aligned chunk of packed elements P .. P + 3 that starts in row i (flat start ti) and runs
+// past its end into the next row(s): the four (row, column) pairs are found first, then their
+// point loads go out together, so one lane pays about one memory latency for the chunk.
+template <int D, int SHIFT>
+__device__ void crossing_chunk(const float *__restrict__ x, uint32_t d, uint32_t n, uint32_t i, uint64_t ti,
+                               uint64_t P, float *__restrict__ out)
+{
+    uint32_t ii[4], jj[4];
+    bool ok[4];
+    uint32_t r = i;
+    uint64_t tr = ti;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; ++q) {
+        while (P + q > tr + r) {  // past the end of row r: into row r + 1
+            tr += r + 1;
+            ++r;
+        }
+        ok[q] = r < n;
+        ii[q] = ok[q] ? r + SHIFT : 0u;
+        jj[q] = ok[q] ? static_cast<uint32_t>(P + q - tr) : 0u;
+    }
+    if (D > 0) {
+        float a[4][D ? D : 1], b[4][D ? D : 1];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+#pragma unroll
+            for (uint32_t k = 0; k < uint32_t(D); ++k) {
+                a[q][k] = __ldg(x + uint64_t(ii[q]) * D + k);
+                b[q][k] = __ldg(x + uint64_t(jj[q]) * D + k);
+            }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+            float s = 0.0f;
+#pragma unroll
+            for (uint32_t k = 0; k < uint32_t(D); ++k) {
+                const float t = a[q][k] - b[q][k];
+                s = fmaf(t, t, s);
+            }
+            if (ok[q]) out[P + q] = sqrtf(s);
+        }
+    } else {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q)
+            if (ok[q]) out[P + q] = direct<0>(x, d, ii[q], jj[q]);
+    }
 }
 
 // n: side of the packed triangle (the number of points minus SHIFT); row i of it pairs point
@@ -152,24 +199,23 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
                     }
                     __syncwarp();
                     const uint32_t j = jb + 4 * lane;
-                    if (j < jhi) {
-                        if (j + 3 <= i) {
-                            __stcs(reinterpret_cast<float4 *>(out + ti + j), *reinterpret_cast<const float4 *>(sres + 4 * lane));
-                        } else {  // the chunk runs past the end of row i into the next row(s)
-                            uint32_t ii = i;
-                            uint64_t tii = ti;
-                            for (uint32_t q = 0; q < 4; ++q) {
-                                const uint64_t P = ti + j + q;
-                                while (P > tii + ii) {
-                                    tii += ii + 1;
-                                    ++ii;
-                                }
-                                if (ii >= n) break;
-                                out[P] = direct<D>(x, d, ii + SHIFT, static_cast<uint32_t>(P - tii));
-                            }
-                        }
-                    }
+                    // a chunk that runs past the end of row i is left to the crossing pass below
+                    if (j < jhi && j + 3 <= i)
+                        __stcs(reinterpret_cast<float4 *>(out + ti + j), *reinterpret_cast<const float4 *>(sres + 4 * lane));
                     __syncwarp();  // sres is rewritten by the next column group
+                }
+            }
+            // crossing pass: lane r takes element row bi rho + r, whose last chunk runs past the row
+            // end unless the row ends on a 16-byte boundary; this run writes it if the chunk's first
+            // element lies in the run's columns of that row
+            if (lane < uint32_t(RHO)) {
+                const uint32_t i = bi * RHO + lane;
+                if (i < n) {
+                    const uint64_t ti = tri(i), E = ti + i + 1;  // flat end (exclusive) of row i
+                    const uint64_t Pc = (E - 1) & ~uint64_t(3);
+                    const uint32_t jc = static_cast<uint32_t>(Pc - ti), jhi = min((bj + run) * RHO, i + 1);
+                    if ((E & 3u) != 0 && Pc >= ti && jc >= jlo && jc < jhi)
+                        crossing_chunk<D, SHIFT>(x, d, n, i, ti, Pc, out);
                 }
             }
         }
