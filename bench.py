@@ -36,8 +36,8 @@ UNIT = "pairs/s"
 # they change the roofline line reports traffic as null until a new capture is taken.
 PROBE_SOURCES = ("td_probe.cu", "td_tiles.cuh", "td_device.cuh", "td_strategies.cuh")
 PROBE_TRAFFIC = {
-    "sources_sha256": "68e269611671a3c7b5f55566316b9244b4cf8924f349931188d6f4eff497cfb9",
-    "bytes_per_launch": {8: 8540543232, 16: 8544728064, 32: 8546507776},
+    "sources_sha256": "1fc765c2f77ad7ef50e5377d15ae2a04a7de8cb1899131aa8e0c9aaa50c837a0",
+    "bytes_per_launch": {8: 8540194304, 16: 8543962112, 32: 8546494464},
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
                "-k regex:k_probe_chunked -s 3 -c 1 "
                "python bench.py --case probe:LTM:chunked:65536:<rho> --steps 1 --warmup 3",
