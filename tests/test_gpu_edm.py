@@ -164,3 +164,24 @@ def test_edm_errors():
         td.td_edm("LTM", "grid", x, 12)          # unsupported rho
     with pytest.raises(td.TDError):
         td.td_edm("REC", "grid", x, 8)           # 10 is not a multiple of 8
+
+
+def test_edm_chunked_random_shapes():
+    """Seeded random shapes: the chunked form (every block strategy it serves) bit-identical to the
+    one-element-per-thread kernel, and its strict form to the element-level strict kernel."""
+    rng = np.random.default_rng(2024)
+    for _ in range(16):
+        n = int(rng.integers(2, 5000))
+        d = int(rng.integers(1, 9))
+        rho = int(rng.choice([8, 16, 32]))
+        xh = synth.uniform_points(n, d, int(rng.integers(1, 1 << 30)))
+        x = torch.from_numpy(xh).cuda()
+        ref, _ = _edm("LTM", "persistent", x, rho)
+        for mapping in ("LTM", "BB", "UTM-BLOCK") + (("REC",) if _cases("REC", rho, n) else ()):
+            got, _ = _edm(mapping, "chunked", x, rho)
+            assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (n, d, rho, mapping)
+        total = n * (n - 1) // 2
+        strict = td.td_edm_strict(x)[:total]
+        for mapping in ("LTM", "BB"):
+            got, _ = td.td_edm_strict_blocks(mapping, x, rho)
+            assert torch.equal(got[:total].view(torch.int32), strict.view(torch.int32)), (n, d, rho, mapping)

@@ -165,3 +165,20 @@ def test_strict_blocks_errors_and_no_ops():
         td.td_edm_strict_blocks("LTM", torch.zeros(10, 9, device="cuda"), 16)  # d > 8: td_edm_strict
     td.td_edm_strict_blocks("LTM", torch.zeros(1, 3, device="cuda"), 16)
     td.td_collide_strict_blocks("LTM", c[:1], r[:1], 32)
+
+
+def test_collide_strict_blocks_random_shapes():
+    """Seeded random sizes and radii ranges: the block-mapped strict bits equal the element-level ones."""
+    rng = np.random.default_rng(77)
+    for _ in range(12):
+        n = int(rng.integers(2, 6000))
+        bits_ = int(rng.integers(4, 21))
+        c, r = synth.spheres(n, seed=int(rng.integers(1, 1 << 30)), coord_bits=bits_, rmin=0,
+                             rmax=int(rng.integers(1, 2049)))
+        ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+        words = td.td_collide_strict_words(n)
+        ref = td.td_collide_strict(ct, rt)[:words].clone()
+        for mapping in ("LTM", "BB"):
+            for rho in (8, 16, 32):
+                got, _ = td.td_collide_strict_blocks(mapping, ct, rt, rho)
+                assert torch.equal(got[:words], ref), (n, bits_, mapping, rho)
