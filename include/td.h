@@ -245,6 +245,17 @@ td_status td_edm_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
  * gets the number of pairs recomputed in the direct form. */
 td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *stream);
 
+/* Self-test of the failure path of the bounded waits (the Gram pipeline's mbarrier waits): one
+ * thread initialises an mbarrier expecting one arrival, arrives on it if `arrive` is 1, then
+ * waits for its first phase with the same bounded wait the pipeline uses, limited to limit_ns.
+ * With arrive = 0 nothing completes the phase, so the wait must run out; the kernel records that
+ * and returns (no trap, no unbounded spin) and the context stays usable.
+ * arrive: 0 or 1; limit_ns: in [1e3, 1e9]; ws: device, uint64[2], 8-byte aligned, scratch;
+ * waited_ns: host, may be NULL, gets the wait's duration read from the device's global timer.
+ * Synchronises `stream`.  Returns TD_ERR_TIMEOUT if the wait ran out, TD_OK if it completed,
+ * TD_ERR_INVALID_ARG for arguments outside the ranges above (nothing launched). */
+td_status td_wait_selftest(uint32_t arrive, uint64_t limit_ns, uint64_t *ws, uint64_t *waited_ns, void *stream);
+
 /* ------------------------------------------------------------------ batched distance maps */
 
 /* Launch configuration of the batched distance map: block side rho (64 or 128) and CTAs per

@@ -442,6 +442,21 @@ td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *str
     return TD_OK;
 }
 
+td_status td_wait_selftest(uint32_t arrive, uint64_t limit_ns, uint64_t *ws, uint64_t *waited_ns, void *stream)
+{
+    g_err[0] = 0;
+    if (arrive > 1) return fail(TD_ERR_INVALID_ARG, "arrive must be 0 or 1 (got %u)", arrive);
+    if (limit_ns < 1000 || limit_ns > 1000000000ull)
+        return fail(TD_ERR_INVALID_ARG, "limit_ns must lie in [1e3, 1e9] (got %llu)", (unsigned long long)limit_ns);
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 7u)) return fail(TD_ERR_INVALID_ARG, "ws must be non-NULL and 8-byte aligned");
+    uint64_t rec[2] = {0, 0};
+    const td_status s = launch_wait_selftest(arrive, limit_ns, ws, rec, static_cast<cudaStream_t>(stream));
+    if (s != TD_OK) return s;
+    if (waited_ns) *waited_ns = rec[1];
+    if (rec[0] != 0) return fail(TD_ERR_TIMEOUT, "td_wait_selftest: the wait ran out after %llu ns", (unsigned long long)rec[1]);
+    return TD_OK;
+}
+
 td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_t *br0, uint32_t *br1, uint64_t *off0,
                        uint64_t *off1)
 {

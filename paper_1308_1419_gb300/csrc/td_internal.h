@@ -66,6 +66,9 @@ size_t batched_workspace_bytes(uint32_t nprob);
 size_t gram_workspace_bytes(uint32_t n, uint32_t d);
 td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *ws, cudaStream_t st);
 td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cudaStream_t st);
+// One bounded mbarrier wait (arrive: whether its phase completes); copies {ran out, ns} to out
+// after synchronising st.
+td_status launch_wait_selftest(uint32_t arrive, uint64_t limit_ns, uint64_t *rec, uint64_t out[2], cudaStream_t st);
 // Library options (td_set_option).
 int option(td_option opt);
 td_status launch_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uint32_t *ij,

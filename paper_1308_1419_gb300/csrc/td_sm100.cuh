@@ -59,14 +59,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Waits for the phase with the given parity to complete; false if it did not within the limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+// Waits for the phase with the given parity to complete; false if it did not within limit_ns
+// nanoseconds (or kSpinLimit polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 0 && global_ns() - t0 > kWaitNs) return false;
+        if ((it & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

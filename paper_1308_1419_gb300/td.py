@@ -84,6 +84,7 @@ _c_edm_strict = _sig("td_edm_strict", _int, _vp, _u32, _u32, _vp, _vp)
 _c_collide_strict = _sig("td_collide_strict", _int, _vp, _vp, _u32, _vp, _vp)
 _c_edm_strict_blocks = _sig("td_edm_strict_blocks", _int, _int, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
 _c_collide_strict_blocks = _sig("td_collide_strict_blocks", _int, _int, _vp, _vp, _u32, _u32, _vp, _stats_p, _vp)
+_c_wait_selftest = _sig("td_wait_selftest", _int, _u32, _u64, _vp, C.POINTER(C.c_uint64), _vp)
 
 
 def _check(status):
@@ -386,6 +387,17 @@ def td_edm_gram_status(ws: torch.Tensor, stream=None) -> int:
     fb = C.c_uint64()
     _check(_c_gram_status(ws.data_ptr() + off, C.byref(fb), _stream(stream)))
     return int(fb.value)
+
+
+def td_wait_selftest(arrive: bool, limit_ns: int, ws: torch.Tensor = None, stream=None) -> int:
+    """One bounded mbarrier wait whose phase completes (arrive) or never does; synchronises and
+    returns the wait's duration in ns, raising TDError (status TD_ERR_TIMEOUT) if it ran out."""
+    if ws is None:
+        ws = torch.zeros(2, dtype=torch.int64, device="cuda")
+    ptr = _dev(ws, torch.int64, 2, "ws")
+    ns = C.c_uint64()
+    _check(_c_wait_selftest(1 if arrive else 0, int(limit_ns), ptr, C.byref(ns), _stream(stream)))
+    return int(ns.value)
 
 
 def td_map_cover(mapping, schedule, N: int, rho: int, count: torch.Tensor = None, stream=None):

@@ -77,6 +77,12 @@ def test_argument_errors_return_before_launch():
     assert td._c_map_dump(0, 100, 0, 10, 256, None) == 2                     # BB has no dump
     assert td._c_ltm_check(0, 10, None, None) == 1
     assert td._c_ltm_check(2**50, 10, 256, None) == 2
+    ns = C.c_uint64()
+    assert td._c_wait_selftest(2, 10**6, 256, C.byref(ns), None) == 1         # arrive not 0/1
+    assert td._c_wait_selftest(0, 999, 256, C.byref(ns), None) == 1           # limit below 1 us
+    assert td._c_wait_selftest(0, 10**9 + 1, 256, C.byref(ns), None) == 1     # limit above 1 s
+    assert td._c_wait_selftest(0, 10**6, None, C.byref(ns), None) == 1        # NULL record
+    assert td._c_wait_selftest(0, 10**6, 260, C.byref(ns), None) == 1         # misaligned record
 
 
 def test_options_validated():
