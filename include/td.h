@@ -320,7 +320,10 @@ td_status td_edm_batched_autotune(uint32_t nprob, const uint32_t *n, const uint3
 
 /* Coverage check of a strategy: every in-domain thread adds 1 to count[T(i) + j]
  * (atomically).  A bijective mapping leaves every entry at exactly its previous value + 1.
- * Same arguments and launch space as td_map_probe; count: device, uint32[T(N)]. */
+ * Same arguments and launch space as td_map_probe; count: device, uint32[T(N)].  Under
+ * TD_SCHED_CHUNKED the chunked probe's own walk adds 1 to each element it would write (chunk
+ * ownership, runs and the chunks that cross row ends included), so a double or missed write of
+ * that schedule shows as a count other than 1. */
 td_status td_map_cover(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho,
                        uint32_t *count, void *stream);
 

@@ -70,11 +70,17 @@ __device__ __forceinline__ uint4 probe4(uint32_t key)
 }
 
 // The chunk of 4 elements starting at row-local j of row i (flat T(i) + j, a multiple of 4).
+// COVER: add 1 to each element's count instead of writing its probe value.
+template <bool COVER>
 __device__ __forceinline__ void probe_chunk(uint32_t *__restrict__ out, uint32_t N, uint32_t i, uint64_t ti,
                                             uint32_t j)
 {
     if (j + 3 <= i) {
-        __stcs(reinterpret_cast<uint4 *>(out + ti + j), probe4(i * N + j));
+        if (COVER) {
+            for (uint32_t k = 0; k < 4; ++k) atomicAdd(out + ti + j + k, 1u);
+        } else {
+            __stcs(reinterpret_cast<uint4 *>(out + ti + j), probe4(i * N + j));
+        }
     } else {  // the chunk runs past the end of row i into the next row(s)
         uint32_t ii = i;
         uint64_t tii = ti;
@@ -85,14 +91,16 @@ __device__ __forceinline__ void probe_chunk(uint32_t *__restrict__ out, uint32_t
                 ++ii;
             }
             if (ii >= N) break;
-            out[P] = splitmix32_mulshift(ii * N + static_cast<uint32_t>(P - tii));
+            if (COVER) atomicAdd(out + P, 1u);
+            else out[P] = splitmix32_mulshift(ii * N + static_cast<uint32_t>(P - tii));
         }
     }
 }
 
 // CPL > 0: strips at most 128 CPL elements wide, each lane's chunks of a row in a fully unrolled
-// loop; CPL = 0: any width, a runtime loop (the wide strips of large launches).
-template <class Tiles, int RHO, int CPL>
+// loop; CPL = 0: any width, a runtime loop (the wide strips of large launches).  COVER: the
+// coverage count under the same schedule (every element must be reached exactly once).
+template <class Tiles, int RHO, int CPL, bool COVER>
 __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, uint32_t S, uint32_t rcap,
                                                      uint32_t *__restrict__ out)
 {
@@ -120,11 +128,11 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
                     for (int c = 0; c < CPL; ++c) {
                         const uint32_t j = c0 + 4 * (lane + 32 * c);
                         if (j >= jhi) break;
-                        probe_chunk(out, N, i, ti, j);
+                        probe_chunk<COVER>(out, N, i, ti, j);
                     }
                 } else {
 #pragma unroll 2
-                    for (uint32_t j = c0 + 4 * lane; j < jhi; j += 128) probe_chunk(out, N, i, ti, j);
+                    for (uint32_t j = c0 + 4 * lane; j < jhi; j += 128) probe_chunk<COVER>(out, N, i, ti, j);
                 }
             }
         }
@@ -138,12 +146,12 @@ __global__ void __launch_bounds__(256) k_probe_chunked(Tiles tiles, uint32_t N, 
 constexpr uint32_t kStripMax = 2048;
 
 
-template <class Tiles, int RHO>
+template <class Tiles, int RHO, bool COVER>
 td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaStream_t st, uint64_t *ctas)
 {
     if (t.units == 0) return TD_OK;
-    auto wide = k_probe_chunked<Tiles, RHO, 0>;
-    auto narrow = k_probe_chunked<Tiles, RHO, 2>;
+    auto wide = k_probe_chunked<Tiles, RHO, 0, COVER>;
+    auto narrow = k_probe_chunked<Tiles, RHO, 2, COVER>;
     const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(wide), 256, 0, ~0ull) * 8;
     const ChunkPlan cp = chunked_plan(t.units, RHO, resident, kStripMax, 8192);
     const auto k = cp.W <= 256 ? narrow : wide;
@@ -154,24 +162,25 @@ td_status launch_chunked_tiles(const Tiles &t, uint32_t N, uint32_t *out, cudaSt
     return launch_status("td probe chunked kernel");
 }
 
-template <int RHO>
+template <int RHO, bool COVER>
 td_status launch_chunked_rho(td_mapping m, uint32_t N, uint32_t *out, const Plan &p, cudaStream_t st, uint64_t *ctas)
 {
     switch (m) {
-    case TD_MAP_LTM: return launch_chunked_tiles<tiles::Ltm, RHO>(tiles::Ltm{tri(p.nb)}, N, out, st, ctas);
+    case TD_MAP_LTM: return launch_chunked_tiles<tiles::Ltm, RHO, COVER>(tiles::Ltm{tri(p.nb)}, N, out, st, ctas);
     case TD_MAP_UTM_BLOCK:
-        return launch_chunked_tiles<tiles::UtmBlk, RHO>(tiles::UtmBlk{tri(p.nb), p.nb}, N, out, st, ctas);
+        return launch_chunked_tiles<tiles::UtmBlk, RHO, COVER>(tiles::UtmBlk{tri(p.nb), p.nb}, N, out, st, ctas);
     case TD_MAP_BB:
-        return launch_chunked_tiles<tiles::Bb, RHO>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, N, out, st, ctas);
+        return launch_chunked_tiles<tiles::Bb, RHO, COVER>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, N, out, st, ctas);
     case TD_MAP_REC: {
         for (uint32_t l = 1; l <= p.rec_k; ++l) {
             const uint32_t sb = (N >> l) / RHO, gx = N / (2 * RHO);
-            const td_status s = launch_chunked_tiles<tiles::RecLevel, RHO>(tiles::RecLevel{uint64_t(gx) * sb, sb, gx},
-                                                                           N, out, st, ctas);
+            const td_status s = launch_chunked_tiles<tiles::RecLevel, RHO, COVER>(
+                tiles::RecLevel{uint64_t(gx) * sb, sb, gx}, N, out, st, ctas);
             if (s != TD_OK) return s;
         }
         const uint32_t mb = p.rec_m / RHO, gx = N / RHO;
-        return launch_chunked_tiles<tiles::RecDiag, RHO>(tiles::RecDiag{uint64_t(gx) * mb, mb, gx}, N, out, st, ctas);
+        return launch_chunked_tiles<tiles::RecDiag, RHO, COVER>(tiles::RecDiag{uint64_t(gx) * mb, mb, gx}, N, out,
+                                                                st, ctas);
     }
     default:
         return fail(TD_ERR_UNSUPPORTED, "the chunked schedule serves the block strategies LTM, BB and REC");
@@ -299,11 +308,13 @@ td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, ui
                        const Plan &p, cudaStream_t st, uint64_t *ctas)
 {
     if (s == TD_SCHED_CHUNKED) {
-        if (cover) return fail(TD_ERR_UNSUPPORTED, "coverage counting uses the GRID or PERSISTENT schedule");
         switch (rho) {
-        case 8: return launch_chunked_rho<8>(m, N, out, p, st, ctas);
-        case 16: return launch_chunked_rho<16>(m, N, out, p, st, ctas);
-        case 32: return launch_chunked_rho<32>(m, N, out, p, st, ctas);
+        case 8: return cover ? launch_chunked_rho<8, true>(m, N, out, p, st, ctas)
+                             : launch_chunked_rho<8, false>(m, N, out, p, st, ctas);
+        case 16: return cover ? launch_chunked_rho<16, true>(m, N, out, p, st, ctas)
+                              : launch_chunked_rho<16, false>(m, N, out, p, st, ctas);
+        case 32: return cover ? launch_chunked_rho<32, true>(m, N, out, p, st, ctas)
+                              : launch_chunked_rho<32, false>(m, N, out, p, st, ctas);
         default: return fail(TD_ERR_INVALID_ARG, "rho must be 8, 16 or 32");
         }
     }

@@ -64,11 +64,11 @@ def test_probe_matches_oracle_small(strategy, sched, rho):
 
 
 @pytest.mark.parametrize("strategy", STRATS)
-@pytest.mark.parametrize("sched", SCHEDS)
+@pytest.mark.parametrize("sched", SCHEDS + ["chunked"])
 def test_cover_exactly_once_small(strategy, sched):
     for rho in [8, 16, 32]:
         for N in [1, 5, 64, 129, 1000, 2048]:
-            if not _supported(strategy, N, rho):
+            if not _supported(strategy, N, rho, sched):
                 continue
             cnt = td.td_map_cover(strategy, sched, N, rho)
             c = cnt.cpu().numpy()
@@ -118,6 +118,24 @@ def test_cover_full_size(strategy):
     N, rho = 65536, 16
     cnt = td.td_map_cover(strategy, "persistent", N, rho)
     assert bool((cnt == 1).all()), strategy
+
+
+@pytest.mark.parametrize("strategy,rho", [("LTM", 8), ("LTM", 16), ("LTM", 32), ("BB", 16), ("UTM-BLOCK", 16),
+                                          ("REC", 16)])
+def test_cover_chunked_full_size(strategy, rho):
+    """The chunked schedule at N = 65536 (wide strips, runs capped at W / rho): each element once."""
+    cnt = td.td_map_cover(strategy, "chunked", 65536, rho)
+    assert bool((cnt == 1).all()), (strategy, rho)
+    del cnt
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("strategy", ["LTM", "BB", "UTM-BLOCK"])
+def test_cover_chunked_ragged(strategy):
+    for rho in [8, 16, 32]:
+        for N in [4097, 12345, 30001]:
+            cnt = td.td_map_cover(strategy, "chunked", N, rho)
+            assert bool((cnt == 1).all()), (strategy, rho, N)
 
 
 def test_ltm_fast_g_exhaustive_below_2_32():
