@@ -26,6 +26,7 @@
 // k = 0 .. d-1 from s = 0, then sqrtf -- bit-identical to td_edm_pair and the tiled kernels.
 #include "td_internal.h"
 #include "td_tiles.cuh"
+#include "td_device.cuh"
 
 namespace td {
 namespace {
@@ -58,7 +59,7 @@ __device__ __forceinline__ float direct(const float *__restrict__ x, uint32_t d,
         const float t = __ldg(a + k) - __ldg(b + k);
         s = fmaf(t, t, s);
     }
-    return sqrtf(s);
+    return dist_sqrt(s);
 }
 
 // The aligned chunk of packed elements P .. P + 3 that starts in row i (flat start ti) and runs
@@ -99,7 +100,7 @@ __device__ void crossing_chunk(const float *__restrict__ x, uint32_t d, uint32_t
                 const float t = a[q][k] - b[q][k];
                 s = fmaf(t, t, s);
             }
-            if (ok[q]) out[P + q] = sqrtf(s);
+            if (ok[q]) out[P + q] = dist_sqrt(s);
         }
     } else {
 #pragma unroll
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
                             }
                         }
 #pragma unroll
-                        for (uint32_t m = 0; m < 4; ++m) sres[lane + 32 * m] = sqrtf(s[m]);
+                        for (uint32_t m = 0; m < 4; ++m) sres[lane + 32 * m] = dist_sqrt(s[m]);
                     }
                     __syncwarp();
                     const uint32_t j = jb + 4 * lane;

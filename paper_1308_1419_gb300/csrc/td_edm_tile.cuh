@@ -246,7 +246,7 @@ struct EdmTile {
 #pragma unroll
             for (int b = 0; b < TN; ++b) {
                 const uint32_t j = j0 + tc + CT * b;
-                if (j <= i) row[j] = sqrtf(acc[a][b]);
+                if (j <= i) row[j] = dist_sqrt(acc[a][b]);
             }
         }
     }

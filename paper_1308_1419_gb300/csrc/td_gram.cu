@@ -96,7 +96,7 @@ __device__ float direct_distance(const float *__restrict__ x, uint32_t d, uint32
         const float t = __ldg(xi + k) - __ldg(xj + k);
         s = fmaf(t, t, s);
     }
-    return sqrtf(s);
+    return dist_sqrt(s);
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(256, 4) k_gram_fix(const float *__restrict__ x
         for (int p = 0; p < FIX_PAIRS; ++p) {
             float s2 = part[p];
             for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            if (lane == 0 && e + p < total) out[tri(pr[p].x) + pr[p].y] = sqrtf(s2);
+            if (lane == 0 && e + p < total) out[tri(pr[p].x) + pr[p].y] = dist_sqrt(s2);
         }
     }
 }

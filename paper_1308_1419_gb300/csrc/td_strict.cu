@@ -14,6 +14,7 @@
 // for bit.
 #include "td_collide.cuh"
 #include "td_internal.h"
+#include "td_device.cuh"
 
 namespace td {
 namespace {
@@ -36,7 +37,7 @@ __device__ __forceinline__ float distance(const float *__restrict__ x, uint32_t 
             s = fmaf(t, t, s);
         }
     }
-    return sqrtf(s);
+    return dist_sqrt(s);
 }
 
 template <int D>

@@ -185,3 +185,23 @@ def test_edm_chunked_random_shapes():
         for mapping in ("LTM", "BB"):
             got, _ = td.td_edm_strict_blocks(mapping, x, rho)
             assert torch.equal(got[:total].view(torch.int32), strict.view(torch.int32)), (n, d, rho, mapping)
+
+
+@pytest.mark.parametrize("sched,rho", [("chunked", 16), ("persistent", 128), ("grid", 16)])
+def test_distance_sqrt_error_one_feature(sched, rho):
+    """At d = 1 the sum is t^2 rounded, t = x_i - x_j in FP32, and the correctly rounded square
+    root of that is exactly |t|; the distance's square root (a hardware approximation) is held to
+    2 units in the last place of |t| over values spread across 60 binades (no underflow or
+    overflow of t^2), and is exact at t = 0."""
+    rng = np.random.default_rng(1308)
+    n = 3000
+    x = (rng.uniform(1.0, 2.0, n) * np.exp2(rng.integers(-30, 31, n)) * rng.choice([-1.0, 1.0], n))
+    x = x.astype(np.float32).reshape(n, 1)
+    got, _ = _edm("LTM", sched, torch.from_numpy(x).cuda(), rho)
+    i, j = np.tril_indices(n)
+    t = np.abs(x[i, 0] - x[j, 0])                      # FP32 subtraction, as on the device
+    gi = got.view(np.int32).astype(np.int64)
+    ti = t.view(np.int32).astype(np.int64)
+    ulp = np.abs(gi - ti)
+    assert np.all(got[t == 0] == 0)
+    assert int(ulp.max()) <= 2, (sched, int(ulp.max()), int((ulp > 0).sum()))
