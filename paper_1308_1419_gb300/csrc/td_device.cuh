@@ -13,20 +13,6 @@ namespace td {
 // T(m) = m(m+1)/2, the row start of row m in the packed lower triangle (Eq. (matrix_indexing)).
 __host__ __device__ __forceinline__ uint64_t tri(uint64_t m) { return (m * (m + 1)) >> 1; }
 
-// The square root that turns a sum of squared differences into a distance (Sec. IV's f(i,j)):
-// the hardware approximation sqrt.approx.f32 (subnormal inputs kept, sqrt(+0) = +0), not the
-// correctly rounded sqrt.rn.f32.  Its error is a couple of units in the last place at most
-// (checked through td_edm at d = 1, where the exact answer is |a - b|), far inside the 2e-6
-// relative tolerance the distance maps are held to, and it saves the refinement steps that
-// took about a quarter of the issue slots of the map at three features.  Every FP32 direct
-// distance in the library goes through it, so all strategies and kernels agree bit for bit.
-__device__ __forceinline__ float dist_sqrt(float s)
-{
-    float r;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(s));
-    return r;
-}
-
 // g(lambda) of Eq. (theorem): i = floor(sqrt(1/4 + 2 lambda) - 1/2), j = lambda - T(i).
 // sqrt(1/4 + 2 lambda) - 1/2 = (sqrt(8 lambda + 1) - 1) / 2.  The square root is taken the
 // LTM-R way (Sec. III-A: sqrt(y) = y * rsqrt(y)), in FP32.  Instead of the paper's

@@ -1,0 +1,22 @@
+// td_dist.cuh -- the square root shared by every FP32 direct distance kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace td {
+
+// The square root that turns a sum of squared differences into a distance (Sec. IV's f(i,j)):
+// the hardware approximation sqrt.approx.f32 (subnormal inputs kept, sqrt(+0) = +0), not the
+// correctly rounded sqrt.rn.f32.  Its error is a couple of units in the last place at most
+// (checked through td_edm at d = 1, where the exact answer is |a - b|), far inside the 2e-6
+// relative tolerance the distance maps are held to, and it saves the refinement steps that
+// took about a quarter of the issue slots of the map at three features.  Every FP32 direct
+// distance in the library goes through it, so all strategies and kernels agree bit for bit.
+__device__ __forceinline__ float dist_sqrt(float s)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return r;
+}
+
+}  // namespace td

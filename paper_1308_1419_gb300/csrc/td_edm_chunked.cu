@@ -26,7 +26,7 @@
 // k = 0 .. d-1 from s = 0, then sqrtf -- bit-identical to td_edm_pair and the tiled kernels.
 #include "td_internal.h"
 #include "td_tiles.cuh"
-#include "td_device.cuh"
+#include "td_dist.cuh"
 
 namespace td {
 namespace {

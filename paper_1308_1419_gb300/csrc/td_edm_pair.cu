@@ -8,7 +8,7 @@
 // schedules give bit-identical results): t = x_i[k] - x_j[k] rounded to FP32, then
 // s = fma(t, t, s) for k = 0, 1, ..., d-1 starting from s = 0, then sqrt rounded to nearest.
 #include "td_strategies.cuh"
-#include "td_device.cuh"
+#include "td_dist.cuh"
 
 namespace td {
 namespace {

@@ -20,6 +20,7 @@
 #pragma once
 
 #include "td_device.cuh"
+#include "td_dist.cuh"
 
 namespace td {
 

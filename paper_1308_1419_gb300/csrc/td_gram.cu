@@ -33,6 +33,7 @@
 #include "td_device.cuh"
 #include "td_internal.h"
 #include "td_sm100.cuh"
+#include "td_dist.cuh"
 
 namespace td {
 namespace {

@@ -14,7 +14,7 @@
 // for bit.
 #include "td_collide.cuh"
 #include "td_internal.h"
-#include "td_device.cuh"
+#include "td_dist.cuh"
 
 namespace td {
 namespace {
