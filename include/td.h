@@ -277,8 +277,9 @@ size_t td_edm_batched_workspace(uint32_t nprob);
  * prefix sum, problems laid heaviest first); one persistent launch walks it, finding each
  * block's problem by binary search over P and its position by g(lambda) (Sec. II-A).
  * n, d: host arrays.  ws: device workspace of td_edm_batched_workspace(nprob) bytes, 16-byte
- * aligned (x_cat and out_cat too).  cfg: NULL = {64, 0}.  The plan upload uses a pageable
- * host-to-device copy (it orders with `stream` but cannot be graph-captured); use
+ * aligned (x_cat and out_cat too).  cfg: NULL = {128, 0} (the faster block side on mixed batches
+ * of 3 to 64 features; td_edm_batched_autotune chooses per batch).  The plan upload uses a
+ * pageable host-to-device copy (it orders with `stream` but cannot be graph-captured); use
  * td_edm_batched_plan + td_edm_batched_run to capture the launch. */
 td_status td_edm_batched(uint32_t nprob, const uint32_t *n, const uint32_t *d, const float *x_cat, float *out_cat,
                          void *ws, size_t ws_bytes, const td_batched_config *cfg, td_launch_stats *stats,

@@ -201,7 +201,7 @@ td_status td_edm_batched(uint32_t nprob, const uint32_t *n, const uint32_t *d, c
     if (stats) *stats = td_launch_stats{0, 0, 0, 0, 0};
     if (nprob == 0) return TD_OK;
     if (!batched_args_ok(nprob, n, d, x_cat, out_cat, ws)) return TD_ERR_INVALID_ARG;
-    const uint32_t rho = cfg ? cfg->rho : 64;
+    const uint32_t rho = cfg ? cfg->rho : 128;
     const uint32_t cps = cfg ? cfg->ctas_per_sm : 0;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     std::vector<unsigned char> host;
@@ -220,7 +220,7 @@ td_status td_edm_batched_autotune(uint32_t nprob, const uint32_t *n, const uint3
 {
     fail(TD_OK, "");
     if (!best) return fail(TD_ERR_INVALID_ARG, "best is NULL");
-    *best = td_batched_config{64, 0};
+    *best = td_batched_config{128, 0};
     if (best_ms) *best_ms = 0.0f;
     if (nprob == 0) return TD_OK;
     if (!batched_args_ok(nprob, n, d, x_cat, out_cat, ws)) return TD_ERR_INVALID_ARG;

@@ -126,7 +126,7 @@ extern "C" td_status td_edm_batched_noalloc(uint32_t nprob, const uint32_t *n, c
         return fail(TD_ERR_INVALID_ARG, "x_cat and out_cat must be 16-byte aligned");
     for (uint32_t q = 0; q < nprob; ++q)
         if (n[q] == 0 || d[q] == 0) return fail(TD_ERR_INVALID_ARG, "problem %u has n = 0 or d = 0", q);
-    const uint32_t rho = cfg ? cfg->rho : 64;
+    const uint32_t rho = cfg ? cfg->rho : 128;
     const uint32_t cps = cfg ? cfg->ctas_per_sm : 0;
     if (rho != 64 && rho != 128) return fail(TD_ERR_INVALID_ARG, "batched rho must be 64 or 128 (got %u)", rho);
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
