@@ -89,6 +89,19 @@ def test_batched_graph_capture_and_autotune():
     assert torch.equal(out[:os_], ref[:os_])
 
 
+def test_batched_default_config_matches_both_block_sides():
+    """cfg NULL (rho = 128) and an explicit rho = 64 give the same bits: the block side changes
+    the schedule, never a sum."""
+    ns, ds, xh = synth.batched_problems(nprob=48, seed=11)
+    x = torch.from_numpy(xh).cuda()
+    _, os_ = td.batched_sizes(ns, ds)
+    dflt, _, st = td.td_edm_batched(ns, ds, x)
+    r64, _, _ = td.td_edm_batched(ns, ds, x, config=(64, 0))
+    r128, _, _ = td.td_edm_batched(ns, ds, x, config=(128, 0))
+    torch.cuda.synchronize()
+    assert torch.equal(dflt[:os_], r128[:os_]) and torch.equal(dflt[:os_], r64[:os_])
+
+
 def test_batched_rejects():
     x = torch.zeros(16, device="cuda")
     with pytest.raises(td.TDError):

@@ -41,3 +41,9 @@ def test_context_usable_after_timeout():
     torch.cuda.synchronize()
     np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32)[:td.td_tri_size(N)], oracle.probe(N))
     assert td.td_wait_selftest(True, 10**6) < 10**6 + 5 * 10**8
+
+
+def test_completed_phase_passes_at_the_shortest_limit():
+    # The phase completes before the wait starts, so even a 1 us limit sees it.
+    for _ in range(3):
+        assert td.td_wait_selftest(True, 1000) < 10**9
