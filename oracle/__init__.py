@@ -53,6 +53,7 @@ _collide_bitpos = _sig("or_collide_bitpos", None, C.c_uint32, C.c_uint32, C.POIN
 _edm_strict = _sig("or_edm_strict", None, _f32p, C.c_uint32, C.c_uint32, _f64p)
 _collide_strict = _sig("or_collide_strict", None, _i32p, _i32p, C.c_uint32, _u32p)
 _fast_rsqrt = _sig("or_fast_rsqrt", C.c_float, C.c_float, C.c_int)
+_fast_rsqrt_fma = _sig("or_fast_rsqrt_fma", C.c_float, C.c_float, C.c_int)
 _ltm_variant = _sig("or_ltm_variant", None, C.c_int, C.c_uint64, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32))
 _ltm_variant_first_fail = _sig("or_ltm_variant_first_fail", C.c_uint64, C.c_int, C.c_uint64, C.c_uint64)
 
@@ -79,7 +80,8 @@ def ltm(lam) -> np.ndarray:
 
 
 # the FP32 evaluations of g that Sec. III-A times (the two with a host definition)
-LTM_X, LTM_N = 1, 2
+# 1, 2: every operation rounded once; 3, 4: the products feeding an addition fused (one rounding)
+LTM_X, LTM_N, LTM_N_FMA, LTM_X_FMA = 1, 2, 3, 4
 
 
 def fast_rsqrt(x: float, steps: int) -> float:
@@ -87,8 +89,14 @@ def fast_rsqrt(x: float, steps: int) -> float:
     return float(_fast_rsqrt(x, steps))
 
 
+def fast_rsqrt_fma(x: float, steps: int) -> float:
+    """The same estimate with each Newton step's product fused into its subtraction (FP32)."""
+    return float(_fast_rsqrt_fma(x, steps))
+
+
 def ltm_variant(variant: int, lam: int):
-    """(i, j) of LTM-X (variant 1) or LTM-N (variant 2) at lambda, in FP32 as defined in td_oracle.c."""
+    """(i, j) of LTM-X (variants 1, 4) or LTM-N (variants 2, 3) at lambda, in FP32 as defined in
+    td_oracle.c (3 and 4: the fused multiply-add evaluations)."""
     i, j = C.c_uint32(), C.c_uint32()
     _ltm_variant(variant, lam, C.byref(i), C.byref(j))
     return i.value, j.value

@@ -96,7 +96,18 @@ void or_ltm_nodiag_many(const uint64_t *lam, uint64_t count, uint32_t *ij)
  *     y = y * (1.5f - ((0.5f * x) * y) * y), then i = trunc((x * y - 0.5f) + 1e-4f): the paper
  *     adds epsilon = 1e-4 to the computation of i here to repair the rounding at row starts.
  * j = lambda - T(i).  The third variant (LTM-R: x * rsqrtf(x) - 0.5 + 1e-4) depends on the
- * device's reciprocal-square-root approximation and has no host definition. */
+ * device's reciprocal-square-root approximation and has no host definition.
+ *
+ * The paper does not say how its compiler evaluated these expressions.  CUDA's compiler fuses a
+ * product feeding an addition or subtraction into one fused multiply-add (rounded once) unless
+ * told not to, so the two variants are also given in that contracted form:
+ *   variant 3 (LTM-N, contracted): the same seed; each Newton step rounds t = (0.5f * x) * y, then
+ *     y = y * fmaf(-t, y, 1.5f) (the product t * y is not rounded before the subtraction); then
+ *     i = trunc(fmaf(x, y, -0.5f) + 1e-4f).
+ *   variant 4 (LTM-X, contracted): x = fmaf(2.0f, (float)lambda, 0.25f); i = trunc(sqrtf(x) - 0.5f).
+ *     2 * (float)lambda is exact in binary floating point, so this x equals variant 1's and the two
+ *     variants agree everywhere; it is kept so that the claim is checked rather than assumed.
+ * fmaf is C99's fused multiply-add, correctly rounded. */
 
 static float bits_to_float(uint32_t b) { float f; memcpy(&f, &b, 4); return f; }
 static uint32_t float_to_bits(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
@@ -112,12 +123,27 @@ float or_fast_rsqrt(float x, int steps)
 
 static uint32_t trunc_u32(float v) { return v <= 0.0f ? 0u : (uint32_t)v; }
 
+/* The inverse-square-root estimate refined by `steps` Newton steps, each in variant 3's
+ * contracted form. */
+float or_fast_rsqrt_fma(float x, int steps)
+{
+    const float h = 0.5f * x;
+    float y = bits_to_float(0x5f3759dfu - (float_to_bits(x) >> 1));
+    for (int k = 0; k < steps; ++k) {
+        const float t = h * y;
+        y = y * fmaf(-t, y, 1.5f);
+    }
+    return y;
+}
+
 void or_ltm_variant(int variant, uint64_t lam, uint32_t *i, uint32_t *j)
 {
     const float x = 0.25f + 2.0f * (float)lam;
     uint32_t r = 0;
     if (variant == 1) r = trunc_u32(sqrtf(x) - 0.5f);
     if (variant == 2) r = trunc_u32((x * or_fast_rsqrt(x, 3) - 0.5f) + 1e-4f);
+    if (variant == 3) r = trunc_u32(fmaf(x, or_fast_rsqrt_fma(x, 3), -0.5f) + 1e-4f);
+    if (variant == 4) r = trunc_u32(sqrtf(fmaf(2.0f, (float)lam, 0.25f)) - 0.5f);
     *i = r;
     *j = (uint32_t)(lam - or_tri(r));
 }

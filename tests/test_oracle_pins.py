@@ -131,6 +131,46 @@ def test_ltm_n_with_epsilon():
         assert oracle.ltm_variant(oracle.LTM_N, lam) == (_row(lam), lam - oracle.tri(_row(lam)))
 
 
+def test_fast_rsqrt_fma_error_matches_lomont():
+    """The Newton steps with their product fused into the subtraction (one rounding fewer) keep
+    Lomont's error figures: 3.44% for the seed, 0.175% after one step, then about squared per
+    step.  A wrong sign or a dropped factor in the fused step breaks the one-step figure."""
+    xs = [float(np.float32(x)) for x in np.linspace(1.0, 4.0, 20001)]
+    errs = [max(abs(oracle.fast_rsqrt_fma(x, s) * math.sqrt(x) - 1.0) for x in xs) for s in range(4)]
+    assert 0.0340 < errs[0] < 0.0345
+    assert 0.00174 < errs[1] < 0.001753
+    assert errs[2] < 5e-6 and errs[3] < 3e-7
+    assert any(oracle.fast_rsqrt_fma(x, 3) != oracle.fast_rsqrt(x, 3) for x in xs)   # a distinct rounding
+
+
+def test_ltm_n_fma_exact_over_the_papers_range():
+    """Sec. III-A: with the epsilon 1e-4, LTM-N computes i exactly for N in [0, 30720], i.e. (rho = 16)
+    for every block index lambda < T(1920) = 1 844 160.  The contracted evaluation, the one a CUDA
+    compiler emits unless told otherwise, meets that claim; the evaluation that rounds every
+    product on its own does not (it first fails inside the range, at the start of a row).  The
+    contracted variant's own first failure lies on a row boundary and is genuine."""
+    end = oracle.tri(30720 // 16)
+    f = oracle.ltm_variant_first_fail(oracle.LTM_N_FMA, 0, 1 << 26)
+    assert end <= f < 1 << 26
+    r = _row(f)
+    assert f in (oracle.tri(r), oracle.tri(r + 1) - 1)
+    assert oracle.ltm_variant(oracle.LTM_N_FMA, f)[0] != r
+    for lam in (0, 1, 2, 3, 4, 5, oracle.tri(1919), end - 1, f - 1):
+        assert oracle.ltm_variant(oracle.LTM_N_FMA, lam) == (_row(lam), lam - oracle.tri(_row(lam)))
+    assert oracle.ltm_variant_first_fail(oracle.LTM_N, 0, end) < end
+
+
+def test_ltm_x_contraction_changes_nothing():
+    """LTM-X has no product to fuse but 2 lambda + 1/4, and 2 (float)lambda is exact in binary
+    floating point, so the fused radicand is the rounded one: both evaluations share their first
+    failure and agree on a dense sample around it and over the whole range below it."""
+    f = oracle.ltm_variant_first_fail(oracle.LTM_X, 0, 1 << 26)
+    assert oracle.ltm_variant_first_fail(oracle.LTM_X_FMA, 0, 1 << 26) == f
+    lams = list(range(f - 2000, f + 2000)) + list(range(1 << 25, (1 << 25) + 2000))
+    for lam in lams:
+        assert oracle.ltm_variant(oracle.LTM_X_FMA, lam) == oracle.ltm_variant(oracle.LTM_X, lam)
+
+
 def test_ltm_nodiag_is_inverse_of_strict_walk():
     # strict walk: row i holds i blocks (row 0 is empty)
     i, j = _enumerate_lower(3000, diag=False)
