@@ -41,13 +41,17 @@ typedef enum {
  * rectangular box (Jung et al.), recursive partition (Ries et al.), and the paper's
  * lower-triangular mapping g(lambda) (Sec. II-A).
  * TD_MAP_LTM evaluates i = floor(sqrt(1/4 + 2 lambda) - 1/2) with an FP32 reciprocal-square-root
- * estimate and an exact integer +-1 fix-up (exact for lambda < 2^40).  The three LTM_* values
- * are the single-precision evaluations Sec. III-A times in its dummy kernel, with no fix-up;
- * with x = 1/4 + 2 lambda rounded to FP32 and every operation rounded to nearest:
+ * estimate and an exact integer +-1 fix-up (exact for lambda < 2^40).  The LTM_* values are
+ * the single-precision evaluations Sec. III-A times in its dummy kernel, with no fix-up; with
+ * x = 1/4 + 2 lambda rounded to FP32 and every operation rounded to nearest (a fused
+ * multiply-add, where written, rounded once):
  *   TD_MAP_LTM_X  i = trunc(sqrt(x) - 1/2)                      (LTM-X);
  *   TD_MAP_LTM_N  y = bits^-1(0x5f3759df - (bits(x) >> 1)), three steps y = y (3/2 - ((x/2) y) y),
  *                 i = trunc(x y - 1/2 + 1e-4)                   (LTM-N, the paper's epsilon);
  *   TD_MAP_LTM_R  i = trunc(x rsqrtf(x) - 1/2 + 1e-4)           (LTM-R, the paper's epsilon);
+ *   TD_MAP_LTM_N_FMA  LTM-N as a CUDA compiler contracts it by default: each step rounds
+ *                 t = (x/2) y and takes y = y fma(-t, y, 3/2); i = trunc(fma(x, y, -1/2) + 1e-4)
+ *                 (exact for lambda < T(1920), i.e. N <= 30720 at rho = 16, as Sec. III-A states);
  * all with j = lambda - T(i).  They are exact only while FP32 resolves the row boundaries
  * (td_ltm_variant_check finds where each stops); they serve td_map_probe, td_map_cover and
  * td_map_dump under GRID or PERSISTENT, and every other call rejects them (TD_ERR_UNSUPPORTED).
@@ -64,7 +68,8 @@ typedef enum {
     TD_MAP_LTM_X = 5,
     TD_MAP_LTM_N = 6,
     TD_MAP_LTM_R = 7,
-    TD_MAP_UTM_BLOCK = 8
+    TD_MAP_UTM_BLOCK = 8,
+    TD_MAP_LTM_N_FMA = 9
 } td_mapping;
 
 /* How the strategy's blocks are issued.
@@ -293,10 +298,11 @@ td_status td_edm_batched_plan(uint32_t nprob, const uint32_t *n, const uint32_t 
 td_status td_edm_batched_run(uint32_t nprob, uint32_t rho, uint64_t total_blocks, const float *x_cat, float *out_cat,
                              const void *ws, uint32_t ctas_per_sm, void *stream);
 
-/* Allocation-free form of td_edm_batched, for callers that cannot allocate device memory: code
- * running while a CUDA graph is being captured, under a memory pool whose budget is already
- * reserved, or in a loop where an allocation (and the synchronisation it may bring) is not
- * allowed.  The paper has no counterpart; this is a packaging of td_edm_batched.
+/* Allocation-free form of td_edm_batched, for callers that cannot allocate device memory: a
+ * serving process whose memory pool already holds all the device memory it may use, a plugin
+ * hosted by a framework that owns every device allocation, or a latency-bound loop where an
+ * allocation (and the device synchronisation it can bring) is not acceptable.  The paper has no
+ * counterpart; this is a packaging of td_edm_batched.
  * Instead of a caller workspace, the launch plan lives in a fixed array of device memory inside
  * the library, sized for at most 1024 problems (about 40 KB; every GPU that loads the library
  * holds it until the process exits).  The call performs no cudaMalloc, cudaFree or other
@@ -340,7 +346,8 @@ td_status td_map_dummy(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho
 /* Dump of a mapping function for unit indices u0 .. u0+count-1 into ij (device,
  * uint32[2*count], pairs (i, j)):
  *   TD_MAP_LTM: unit = block index lambda, (i, j) = g(lambda) of Eq. (theorem); N unused.
- *   TD_MAP_LTM_X, TD_MAP_LTM_N, TD_MAP_LTM_R: the same with that FP32 evaluation (lambda < 2^48).
+ *   TD_MAP_LTM_X, TD_MAP_LTM_N, TD_MAP_LTM_N_FMA, TD_MAP_LTM_R: the same with that FP32 evaluation
+ *               (lambda < 2^48).
  *   TD_MAP_UTM_BLOCK: unit = block index lambda < T(N), (i, j) = its block for a block triangle of
  *               side N (N < 2^30).
  *   TD_MAP_UTM: unit = thread index k < T(N), (i, j) = the UTM pair of Sec. III-B for the
@@ -361,7 +368,7 @@ td_status td_map_dump(td_mapping m, uint32_t N, uint64_t u0, uint64_t count, uin
 td_status td_ltm_check(uint64_t lam0, uint64_t count, uint64_t *result, void *stream);
 
 /* The same count for any evaluation of g: m in {TD_MAP_LTM, TD_MAP_LTM_X, TD_MAP_LTM_N,
- * TD_MAP_LTM_R} (td_ltm_check is m = TD_MAP_LTM).  Same result convention and range limit;
+ * TD_MAP_LTM_N_FMA, TD_MAP_LTM_R} (td_ltm_check is m = TD_MAP_LTM).  Same result convention and range limit;
  * other m: TD_ERR_UNSUPPORTED. */
 td_status td_ltm_variant_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t *result, void *stream);
 

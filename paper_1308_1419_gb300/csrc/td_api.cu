@@ -123,6 +123,7 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
     case TD_MAP_LTM:
     case TD_MAP_LTM_X:
     case TD_MAP_LTM_N:
+    case TD_MAP_LTM_N_FMA:
     case TD_MAP_LTM_R:
     case TD_MAP_UTM_BLOCK:
         p.blocks = p.useful = tri(nb);
@@ -512,7 +513,7 @@ td_status td_ltm_variant_check(td_mapping m, uint64_t lam0, uint64_t count, uint
 {
     g_err[0] = 0;
     if (m != TD_MAP_LTM && !ltm_variant(m))
-        return fail(TD_ERR_UNSUPPORTED, "td_ltm_variant_check takes LTM, LTM_X, LTM_N or LTM_R");
+        return fail(TD_ERR_UNSUPPORTED, "td_ltm_variant_check takes LTM, LTM_X, LTM_N, LTM_N_FMA or LTM_R");
     if (!result) return fail(TD_ERR_INVALID_ARG, "result is NULL");
     if (!aligned16(result)) return fail(TD_ERR_INVALID_ARG, "result must be 16-byte aligned");
     if (lam0 + count < lam0 || lam0 + count > (uint64_t(1) << 48))

@@ -65,8 +65,9 @@ struct LtmExact {
 };
 
 // The single-precision evaluations of i = floor(sqrt(1/4 + 2 lambda) - 1/2) that Sec. III-A
-// times in the dummy kernel, each written with explicitly rounded operations (no contraction)
-// so that it is one well-defined FP32 function; none carries a fix-up, so each is exact only
+// times in the dummy kernel, each written with explicitly rounded operations (fused multiply-adds
+// only where written, in LtmNewtonFma) so that it is one well-defined FP32 function; none carries
+// a fix-up, so each is exact only
 // while FP32 resolves the row boundaries.  j = lambda - T(i) in 64-bit integers, truncated.
 __device__ __forceinline__ float ltm_radicand(uint64_t lam)  // x = 1/4 + 2 lambda, rounded
 {
@@ -93,6 +94,22 @@ struct LtmNewton {
 #pragma unroll
         for (int k = 0; k < 3; ++k) y = __fmul_rn(y, __fsub_rn(1.5f, __fmul_rn(__fmul_rn(h, y), y)));
         i = __float2uint_rz(__fadd_rn(__fsub_rn(__fmul_rn(x, y), 0.5f), 1e-4f));
+        j = static_cast<uint32_t>(lam - tri(i));
+    }
+};
+
+// LTM-N as a CUDA compiler contracts it by default: each Newton step rounds t = (x/2) y, then fuses
+// t y into the subtraction from 3/2 (y <- y fma(-t, y, 3/2)), and x y - 1/2 is one fused
+// multiply-add; epsilon 1e-4 is added after it.  The paper's statement that LTM-N is exact for
+// N <= 30720 at rho = 16 (lambda < T(1920)) holds for this evaluation and not for LtmNewton's.
+struct LtmNewtonFma {
+    __device__ __forceinline__ void operator()(uint64_t lam, uint32_t &i, uint32_t &j) const
+    {
+        const float x = ltm_radicand(lam), h = __fmul_rn(0.5f, x);
+        float y = __int_as_float(0x5f3759df - (__float_as_int(x) >> 1));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) y = __fmul_rn(y, __fmaf_rn(-__fmul_rn(h, y), y, 1.5f));
+        i = __float2uint_rz(__fadd_rn(__fmaf_rn(x, y, -0.5f), 1e-4f));
         j = static_cast<uint32_t>(lam - tri(i));
     }
 };

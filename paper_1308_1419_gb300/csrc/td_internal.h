@@ -77,7 +77,10 @@ td_status launch_dummy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, ui
                        cudaStream_t st, uint64_t *ctas);
 td_status launch_ltm_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t *result, cudaStream_t st);
 // The FP32 evaluations of g timed in Sec. III-A (probe, cover and dump only).
-inline bool ltm_variant(td_mapping m) { return m == TD_MAP_LTM_X || m == TD_MAP_LTM_N || m == TD_MAP_LTM_R; }
+inline bool ltm_variant(td_mapping m)
+{
+    return m == TD_MAP_LTM_X || m == TD_MAP_LTM_N || m == TD_MAP_LTM_N_FMA || m == TD_MAP_LTM_R;
+}
 // Strategies whose unit is a whole square block and that have a tile source (td_tiles.cuh).
 inline bool block_strategy(td_mapping m)
 {

@@ -201,6 +201,8 @@ __global__ void k_map_dump(int m, uint32_t N, uint32_t W, uint64_t u0, uint64_t 
             LtmSqrt{}(u, i, j);
         } else if (m == TD_MAP_LTM_N) {
             LtmNewton{}(u, i, j);
+        } else if (m == TD_MAP_LTM_N_FMA) {
+            LtmNewtonFma{}(u, i, j);
         } else if (m == TD_MAP_LTM_R) {
             LtmRsqrtEps{}(u, i, j);
         } else if (m == TD_MAP_UTM_BLOCK) {
@@ -267,6 +269,7 @@ td_status launch_variant(td_mapping m, bool P, uint32_t N, uint32_t rho, Body bo
     switch (m) {
     case TD_MAP_LTM_X: return launch_variant_map<LtmSqrt>(P, N, rho, body, p, st, ctas);
     case TD_MAP_LTM_N: return launch_variant_map<LtmNewton>(P, N, rho, body, p, st, ctas);
+    case TD_MAP_LTM_N_FMA: return launch_variant_map<LtmNewtonFma>(P, N, rho, body, p, st, ctas);
     case TD_MAP_LTM_R: return launch_variant_map<LtmRsqrtEps>(P, N, rho, body, p, st, ctas);
     default: return fail(TD_ERR_INVALID_ARG, "not an LTM variant (%d)", int(m));
     }
@@ -346,8 +349,9 @@ td_status launch_ltm_check(td_mapping m, uint64_t lam0, uint64_t count, uint64_t
     case TD_MAP_LTM: k_ltm_check<LtmExact><<<g, 256, 0, st>>>(lam0, count, res); break;
     case TD_MAP_LTM_X: k_ltm_check<LtmSqrt><<<g, 256, 0, st>>>(lam0, count, res); break;
     case TD_MAP_LTM_N: k_ltm_check<LtmNewton><<<g, 256, 0, st>>>(lam0, count, res); break;
+    case TD_MAP_LTM_N_FMA: k_ltm_check<LtmNewtonFma><<<g, 256, 0, st>>>(lam0, count, res); break;
     case TD_MAP_LTM_R: k_ltm_check<LtmRsqrtEps><<<g, 256, 0, st>>>(lam0, count, res); break;
-    default: return fail(TD_ERR_UNSUPPORTED, "td_ltm_variant_check takes LTM, LTM_X, LTM_N or LTM_R");
+    default: return fail(TD_ERR_UNSUPPORTED, "td_ltm_variant_check takes LTM, LTM_X, LTM_N, LTM_N_FMA or LTM_R");
     }
     return launch_status("td_ltm_check kernel");
 }

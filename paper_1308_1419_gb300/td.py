@@ -17,7 +17,8 @@ if not os.path.exists(_PATH):
                       "needs nvcc with sm_103a support)")
 lib = C.CDLL(_PATH)
 
-MAPPINGS = {"BB": 0, "UTM": 1, "RB": 2, "REC": 3, "LTM": 4, "LTM-X": 5, "LTM-N": 6, "LTM-R": 7, "UTM-BLOCK": 8}
+MAPPINGS = {"BB": 0, "UTM": 1, "RB": 2, "REC": 3, "LTM": 4, "LTM-X": 5, "LTM-N": 6, "LTM-R": 7, "UTM-BLOCK": 8,
+            "LTM-N-FMA": 9}
 SCHEDULES = {"grid": 0, "persistent": 1, "chunked": 2}
 STATUS = {0: "TD_OK", 1: "TD_ERR_INVALID_ARG", 2: "TD_ERR_UNSUPPORTED", 3: "TD_ERR_CUDA", 4: "TD_ERR_TIMEOUT"}
 

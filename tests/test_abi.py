@@ -71,7 +71,7 @@ def test_argument_errors_return_before_launch():
     assert td._c_map_probe(4, 1, 1024, 16, None, C.byref(st), None) == 1     # NULL output
     assert td._c_map_probe(4, 1, 1024, 16, 8, C.byref(st), None) == 1        # misaligned
     assert td._c_map_probe(3, 1, 100, 8, 256, C.byref(st), None) == 2        # REC needs N % rho == 0
-    assert td._c_map_probe(9, 1, 100, 8, 256, C.byref(st), None) == 1        # unknown mapping
+    assert td._c_map_probe(10, 1, 100, 8, 256, C.byref(st), None) == 1       # unknown mapping
     assert td._c_map_probe(4, 5, 100, 8, 256, C.byref(st), None) == 1        # unknown schedule
     assert td._c_map_probe(4, 1, 0, 16, None, C.byref(st), None) == 0        # N = 0 is a no-op
     assert td._c_map_dump(0, 100, 0, 10, 256, None) == 2                     # BB has no dump

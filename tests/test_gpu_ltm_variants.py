@@ -1,5 +1,6 @@
 """GPU parity of the FP32 evaluations of g that Sec. III-A times (LTM-X, LTM-N, LTM-R): the
-device dump of LTM-X and LTM-N equals the oracle's FP32 definitions bit for bit, the device
+device dump of LTM-X and LTM-N (rounded per operation, and as a compiler contracts it into fused
+multiply-adds) equals the oracle's FP32 definitions bit for bit, the device
 check finds the oracle's first failing lambda, and the probe driven by a variant is exact below
 that lambda and misses elements above it.  LTM-R rests on the device's reciprocal square root,
 so its first failure is checked for consistency: a genuine failure, with none before it."""
@@ -18,7 +19,7 @@ if not torch.cuda.is_available():
 
 from paper_1308_1419_gb300 import td  # noqa: E402
 
-VARIANT = {"LTM-X": oracle.LTM_X, "LTM-N": oracle.LTM_N}
+VARIANT = {"LTM-X": oracle.LTM_X, "LTM-N": oracle.LTM_N, "LTM-N-FMA": oracle.LTM_N_FMA}
 
 
 def _row(lam):
@@ -38,7 +39,7 @@ def _check(mapping, lam0, count):
     return int(r[0]), int(r[1]) & (2**64 - 1)
 
 
-@pytest.mark.parametrize("mapping", ["LTM-X", "LTM-N"])
+@pytest.mark.parametrize("mapping", ["LTM-X", "LTM-N", "LTM-N-FMA"])
 def test_variant_dump_matches_oracle_fp32(mapping):
     v = VARIANT[mapping]
     first = oracle.ltm_variant_first_fail(v, 0, 1 << 26)
@@ -49,7 +50,7 @@ def test_variant_dump_matches_oracle_fp32(mapping):
     assert np.array_equal(got, want), mapping
 
 
-@pytest.mark.parametrize("mapping", ["LTM-X", "LTM-N"])
+@pytest.mark.parametrize("mapping", ["LTM-X", "LTM-N", "LTM-N-FMA"])
 def test_variant_check_finds_oracle_first_failure(mapping):
     first = oracle.ltm_variant_first_fail(VARIANT[mapping], 0, 1 << 26)
     bad, f = _check(mapping, 0, 1 << 26)
@@ -67,7 +68,7 @@ def test_exact_g_and_ltm_r_checks():
         assert _check("LTM-R", 0, f) == (0, 2**64 - 1)
 
 
-@pytest.mark.parametrize("mapping", ["LTM-X", "LTM-N", "LTM-R"])
+@pytest.mark.parametrize("mapping", ["LTM-X", "LTM-N", "LTM-N-FMA", "LTM-R"])
 def test_variant_probe_exact_below_first_failure(mapping):
     N, rho = 4096, 16                                       # lambda < T(256): below every failure
     want = oracle.probe(N)
@@ -94,14 +95,14 @@ def test_variant_probe_misses_elements_past_first_failure():
 
 def test_variants_rejected_elsewhere():
     x = torch.zeros(64, 3, device="cuda")
-    for mapping in ("LTM-X", "LTM-N", "LTM-R"):
+    for mapping in ("LTM-X", "LTM-N", "LTM-N-FMA", "LTM-R"):
         with pytest.raises(td.TDError):
             td.td_edm(mapping, "grid", x, 16)
         with pytest.raises(td.TDError):
             td.td_map_probe(mapping, "chunked", 1024, 16)
 
 
-@pytest.mark.parametrize("mapping", ["BB", "UTM", "RB", "REC", "LTM", "LTM-X", "LTM-N", "LTM-R"])
+@pytest.mark.parametrize("mapping", ["BB", "UTM", "RB", "REC", "LTM", "LTM-X", "LTM-N", "LTM-N-FMA", "LTM-R"])
 def test_dummy_kernel_maps_and_writes_nothing(mapping):
     """The map-only dummy kernel: every strategy launches its plan's blocks and leaves the sink."""
     sentinel = 12345
@@ -114,3 +115,16 @@ def test_dummy_kernel_maps_and_writes_nothing(mapping):
             torch.cuda.synchronize()
             assert int(sink[0]) == sentinel, (mapping, sched)
             assert st == td.td_plan(mapping, sched, N, rho) | {"ctas": st["ctas"]}
+
+
+def test_ltm_n_fma_probe_exact_over_the_papers_range():
+    """Sec. III-A: LTM-N with its epsilon is exact for N up to 30720 at rho = 16.  The contracted
+    evaluation writes that whole triangle correctly through the probe, under both schedules, and
+    the device check finds no failure over its block indices; the per-operation rounding fails there."""
+    N, rho = 30720, 16
+    want = oracle.probe(N)
+    for sched in ("grid", "persistent"):
+        out, _ = td.td_map_probe("LTM-N-FMA", sched, N, rho)
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), want), sched
+    assert _check("LTM-N-FMA", 0, oracle.tri(N // rho)) == (0, 2**64 - 1)
+    assert _check("LTM-N", 0, oracle.tri(N // rho))[0] > 0
