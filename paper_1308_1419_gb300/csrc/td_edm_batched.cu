@@ -21,27 +21,39 @@
 
 namespace td {
 
-struct BatchMeta {  // one problem, in launch-space order (16-byte aligned)
-    uint64_t x_off;    // first float of the problem's points in x_cat
-    uint64_t out_off;  // first float of the problem's packed triangle in out_cat
-    uint32_t n, d;
-    uint32_t pad0, pad1;
-};
-static_assert(sizeof(BatchMeta) == 32, "BatchMeta layout");
-
-struct BatchHeader {  // first 64 bytes of the workspace
-    uint64_t magic;
-    uint64_t total_blocks;
-    uint32_t nprob, rho;
-    uint32_t pad[10];
-};
-static_assert(sizeof(BatchHeader) == 64, "BatchHeader layout");
-
-static const uint64_t kMagic = 0x7464626174636831ull;  // "tdbatch1"
-
 size_t batched_workspace_bytes(uint32_t nprob)
 {
     return sizeof(BatchHeader) + (size_t(nprob) + 1) * sizeof(uint64_t) + size_t(nprob) * sizeof(BatchMeta);
+}
+
+uint64_t batched_weight(uint32_t n, uint32_t d, uint32_t rho) { return tri((n + rho - 1) / rho) * d; }
+
+uint64_t batched_fill_image(uint32_t nprob, const uint32_t *n, const uint32_t *d, uint32_t rho, const uint32_t *order,
+                            uint64_t *x_off, uint64_t *out_off, unsigned char *img)
+{
+    uint64_t xacc = 0, oacc = 0;
+    for (uint32_t q = 0; q < nprob; ++q) {  // offsets in input (concatenation) order
+        x_off[q] = xacc;
+        out_off[q] = oacc;
+        xacc += uint64_t(n[q]) * d[q];
+        oacc += tri(n[q]);
+    }
+    auto *hdr = reinterpret_cast<BatchHeader *>(img);
+    auto *prefix = reinterpret_cast<uint64_t *>(img + sizeof(BatchHeader));
+    auto *meta = reinterpret_cast<BatchMeta *>(img + sizeof(BatchHeader) + (size_t(nprob) + 1) * sizeof(uint64_t));
+    uint64_t acc = 0;
+    for (uint32_t s = 0; s < nprob; ++s) {
+        const uint32_t q = order[s];
+        prefix[s] = acc;
+        acc += tri((n[q] + rho - 1) / rho);
+        meta[s] = BatchMeta{x_off[q], out_off[q], n[q], d[q], 0, 0};
+    }
+    prefix[nprob] = acc;
+    hdr->magic = kBatchMagic;
+    hdr->total_blocks = acc;
+    hdr->nprob = nprob;
+    hdr->rho = rho;
+    return acc;
 }
 
 namespace {
@@ -101,35 +113,15 @@ td_status batched_plan(uint32_t nprob, const uint32_t *n, const uint32_t *d, uin
     if (rho != 64 && rho != 128) return fail(TD_ERR_INVALID_ARG, "batched rho must be 64 or 128 (got %u)", rho);
     if (ws_bytes < batched_workspace_bytes(nprob)) return fail(TD_ERR_INVALID_ARG, "workspace too small");
     std::vector<uint64_t> xo(nprob), oo(nprob), weight(nprob);
-    uint64_t xacc = 0, oacc = 0;
     for (uint32_t q = 0; q < nprob; ++q) {
         if (n[q] == 0 || d[q] == 0) return fail(TD_ERR_INVALID_ARG, "problem %u has n = 0 or d = 0", q);
-        xo[q] = xacc;
-        oo[q] = oacc;
-        xacc += uint64_t(n[q]) * d[q];
-        oacc += tri(n[q]);
-        const uint64_t nb = (n[q] + rho - 1) / rho;
-        weight[q] = tri(nb) * d[q];
+        weight[q] = batched_weight(n[q], d[q], rho);
     }
     std::vector<uint32_t> order(nprob);
     std::iota(order.begin(), order.end(), 0u);
     std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return weight[a] > weight[b]; });
     host.assign(batched_workspace_bytes(nprob), 0);
-    auto *hdr = reinterpret_cast<BatchHeader *>(host.data());
-    auto *prefix = reinterpret_cast<uint64_t *>(host.data() + sizeof(BatchHeader));
-    auto *meta = reinterpret_cast<BatchMeta *>(host.data() + sizeof(BatchHeader) + (size_t(nprob) + 1) * 8);
-    uint64_t acc = 0;
-    for (uint32_t s = 0; s < nprob; ++s) {
-        const uint32_t q = order[s];
-        prefix[s] = acc;
-        acc += tri((n[q] + rho - 1) / rho);
-        meta[s] = BatchMeta{xo[q], oo[q], n[q], d[q], 0, 0};
-    }
-    prefix[nprob] = acc;
-    hdr->magic = kMagic;
-    hdr->total_blocks = acc;
-    hdr->nprob = nprob;
-    hdr->rho = rho;
+    const uint64_t acc = batched_fill_image(nprob, n, d, rho, order.data(), xo.data(), oo.data(), host.data());
     *total_out = acc;
     return cuda_status(cudaMemcpyAsync(ws, host.data(), host.size(), cudaMemcpyHostToDevice, st),
                        "td_edm_batched_plan upload");

@@ -1,11 +1,11 @@
 // td_edm_batched_noalloc.cu -- td_edm_batched for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA graph capture, under a
-// memory pool that is already fully reserved, or in a real-time loop where an allocation (and
-// the device synchronisation it can cause) is not allowed.  td_edm_batched needs a small device
-// workspace for its launch plan; this variant keeps that plan in a fixed array of device memory
-// that is part of the library itself, so the call allocates nothing -- no cudaMalloc, no
-// cudaFree, no host allocation.
+// Some callers cannot call cudaMalloc: a serving process whose memory pool already holds every
+// byte of device memory it may use, a plugin hosted by a framework that owns all device
+// allocations, or a latency-bound loop where an allocation (and the device synchronisation it can
+// bring) is not acceptable.  td_edm_batched needs a small device workspace for its launch plan;
+// this variant keeps that plan in a fixed array of device memory that is part of the library
+// itself, so the call allocates nothing -- no cudaMalloc, no cudaFree, no host allocation.
 //
 // The array holds the plan of at most kMaxProblems problems (about 40 KB).  Every GPU that
 // loads the library holds it until the process exits.  All calls share it and it keeps the last
@@ -32,16 +32,15 @@ td_status batched_run(uint32_t nprob, uint32_t rho, uint64_t total, const float 
 namespace {
 
 constexpr uint32_t kMaxProblems = 1024;
-constexpr size_t kHeaderBytes = 64;
-constexpr size_t kMetaBytes = 32;
-constexpr size_t kScratchBytes = kHeaderBytes + (size_t(kMaxProblems) + 1) * 8 + size_t(kMaxProblems) * kMetaBytes;
+constexpr size_t kScratchBytes =
+    sizeof(BatchHeader) + (size_t(kMaxProblems) + 1) * sizeof(uint64_t) + size_t(kMaxProblems) * sizeof(BatchMeta);
 
 static __device__ __align__(256) unsigned char g_plan_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;                                   // guards the host staging and the address cache
 void *g_scratch_addr[kMaxDevices] = {};            // device address of g_plan_scratch, per device
-unsigned char g_stage[kScratchBytes];              // host image of the plan
+alignas(16) unsigned char g_stage[kScratchBytes];  // host image of the plan
 uint32_t g_order[kMaxProblems];
 uint64_t g_xoff[kMaxProblems], g_ooff[kMaxProblems];
 
@@ -61,48 +60,22 @@ td_status scratch_address(void **out)
     return TD_OK;
 }
 
-// Host image of the plan in the layout td_edm_batched_run reads: a 64-byte header
-// {magic, total blocks, nprob, rho}, the exclusive prefix sums of the block counts T(ceil(n/rho))
-// in launch-space order (heaviest problem first, by T(nb) d, ties in input order), then one
-// 32-byte record {x offset, out offset, n, d} per problem in that order.
+// Host image of the plan (the layout td_edm_batched_run reads), problems laid heaviest first with
+// ties in input order -- td_edm_batched's order -- by a stable insertion sort, which needs no
+// allocation.
 uint64_t stage_plan(uint32_t nprob, const uint32_t *n, const uint32_t *d, uint32_t rho)
 {
-    uint64_t xacc = 0, oacc = 0;
     for (uint32_t q = 0; q < nprob; ++q) {
-        g_xoff[q] = xacc;
-        g_ooff[q] = oacc;
-        xacc += uint64_t(n[q]) * d[q];
-        oacc += tri(n[q]);
-    }
-    auto weight = [&](uint32_t q) { return tri((n[q] + rho - 1) / rho) * d[q]; };
-    for (uint32_t q = 0; q < nprob; ++q) {  // stable insertion sort, heaviest first
         uint32_t k = q;
-        const uint64_t w = weight(q);
-        while (k > 0 && weight(g_order[k - 1]) < w) {
+        const uint64_t w = batched_weight(n[q], d[q], rho);
+        while (k > 0 && batched_weight(n[g_order[k - 1]], d[g_order[k - 1]], rho) < w) {
             g_order[k] = g_order[k - 1];
             --k;
         }
         g_order[k] = q;
     }
-    std::memset(g_stage, 0, kScratchBytes);
-    auto *prefix = reinterpret_cast<uint64_t *>(g_stage + kHeaderBytes);
-    unsigned char *meta = g_stage + kHeaderBytes + (size_t(nprob) + 1) * 8;
-    uint64_t acc = 0;
-    for (uint32_t s = 0; s < nprob; ++s) {
-        const uint32_t q = g_order[s];
-        prefix[s] = acc;
-        acc += tri((n[q] + rho - 1) / rho);
-        const uint32_t nd[4] = {n[q], d[q], 0, 0};
-        std::memcpy(meta + size_t(s) * kMetaBytes, &g_xoff[q], 8);
-        std::memcpy(meta + size_t(s) * kMetaBytes + 8, &g_ooff[q], 8);
-        std::memcpy(meta + size_t(s) * kMetaBytes + 16, nd, 16);
-    }
-    prefix[nprob] = acc;
-    const uint64_t hdr[2] = {0x7464626174636831ull, acc};
-    const uint32_t hdr2[2] = {nprob, rho};
-    std::memcpy(g_stage, hdr, 16);
-    std::memcpy(g_stage + 16, hdr2, 8);
-    return acc;
+    std::memset(g_stage, 0, batched_workspace_bytes(nprob));
+    return batched_fill_image(nprob, n, d, rho, g_order, g_xoff, g_ooff, g_stage);
 }
 
 }  // namespace
@@ -135,7 +108,7 @@ extern "C" td_status td_edm_batched_noalloc(uint32_t nprob, const uint32_t *n, c
     td_status s = scratch_address(&ws);
     if (s != TD_OK) return s;
     const uint64_t total = stage_plan(nprob, n, d, rho);
-    const size_t bytes = kHeaderBytes + (size_t(nprob) + 1) * 8 + size_t(nprob) * kMetaBytes;
+    const size_t bytes = batched_workspace_bytes(nprob);
     // a pageable source: the copy returns once g_stage has been read, so the next call may reuse it
     s = cuda_status(cudaMemcpyAsync(ws, g_stage, bytes, cudaMemcpyHostToDevice, st),
                     "td_edm_batched_noalloc plan upload");

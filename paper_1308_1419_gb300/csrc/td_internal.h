@@ -62,7 +62,32 @@ td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t
                            float *out, const Plan &p, bool x2, cudaStream_t st, uint64_t *ctas);
 td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
                          uint32_t *table, cudaStream_t st, uint64_t *ctas);
+// Plan of the batched distance map, as td_edm_batched_run reads it from device memory: a
+// BatchHeader, the nprob + 1 exclusive prefix sums (uint64) of the problems' block counts
+// T(ceil(n/rho)) in launch-space order, then one BatchMeta per problem in that order.
+struct BatchMeta {     // one problem, in launch-space order
+    uint64_t x_off;    // first float of the problem's points in x_cat
+    uint64_t out_off;  // first float of the problem's packed triangle in out_cat
+    uint32_t n, d;
+    uint32_t pad0, pad1;
+};
+static_assert(sizeof(BatchMeta) == 32, "BatchMeta layout");
+struct BatchHeader {   // first 64 bytes of the plan
+    uint64_t magic;
+    uint64_t total_blocks;
+    uint32_t nprob, rho;
+    uint32_t pad[10];
+};
+static_assert(sizeof(BatchHeader) == 64, "BatchHeader layout");
+constexpr uint64_t kBatchMagic = 0x7464626174636831ull;  // "tdbatch1"
 size_t batched_workspace_bytes(uint32_t nprob);
+// Launch-space weight of a problem (block count times features): problems are laid heaviest first.
+uint64_t batched_weight(uint32_t n, uint32_t d, uint32_t rho);
+// Writes the plan image (batched_workspace_bytes(nprob) bytes at img, zeroed by the caller) for
+// the problems taken in launch-space order order[0 .. nprob); returns the total block count.
+// x_off / out_off: scratch of nprob entries each.  Allocates nothing.
+uint64_t batched_fill_image(uint32_t nprob, const uint32_t *n, const uint32_t *d, uint32_t rho, const uint32_t *order,
+                            uint64_t *x_off, uint64_t *out_off, unsigned char *img);
 size_t gram_workspace_bytes(uint32_t n, uint32_t d);
 td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *ws, cudaStream_t st);
 td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cudaStream_t st);
