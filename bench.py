@@ -137,21 +137,67 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_sample(seconds_target=12.0):
-    """Oracle probe on whole rows of the lower half of the N = 65536 triangle (rows 32768 ..,
-    starting over there when the triangle ends) until ~seconds_target elapse."""
+def host_cores():
+    """Host cores this process may run on (the oracle's threads use all of them)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_rate(items, seconds, threads):
+    """Throughput of the CPU oracle: `threads` host threads take work items (fn, units) in turn,
+    cycling through the list, until `seconds` have passed; every item is an independent call into
+    the C oracle, which runs with the interpreter lock released.  Returns (units/s, units, s)."""
+    import itertools
+    import threading
+    lock = threading.Lock()
+    order = itertools.cycle(range(len(items)))
+    done = [0]
+    t0 = time.perf_counter()
+    stop = t0 + seconds
+
+    def worker():
+        while time.perf_counter() < stop:
+            with lock:
+                k = next(order)
+            fn, units = items[k]
+            fn()
+            with lock:
+                done[0] += units
+
+    pool = [threading.Thread(target=worker) for _ in range(threads)]
+    for t in pool:
+        t.start()
+    for t in pool:
+        t.join()
+    dt = time.perf_counter() - t0
+    return done[0] / dt, done[0], dt
+
+
+def cpu_baseline_entry(items, seconds, unit, sample):
+    """The oracle on one host core and on all of them (threads over disjoint work items)."""
+    cores = host_cores()
+    v1, u1, t1 = cpu_rate(items, seconds, 1)
+    vn, un, tn = cpu_rate(items, seconds, cores)
+    return {"value": vn, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample,
+            "one_core": {"value": v1, "cores": 1, "units": u1, "seconds": t1},
+            "all_cores": {"value": vn, "cores": cores, "units": un, "seconds": tn}}
+
+
+def probe_items(rows=256):
+    """Work items of the headline's CPU sample: the oracle probe on whole rows of the lower half of
+    the N = 65536 triangle (rows 32768 .. 65535, `rows` at a time)."""
     import oracle
     N = 65536
-    rows, pairs, t0 = 256, 0, time.perf_counter()
-    i0 = N // 2
-    while time.perf_counter() - t0 < seconds_target:
-        if i0 + rows > N:
-            i0 = N // 2
-        oracle.probe(N, i0, i0 + rows)
-        pairs += tri(i0 + rows) - tri(i0)
-        i0 += rows
-    dt = time.perf_counter() - t0
-    return pairs / dt, pairs, dt
+    return [((lambda a=i0: oracle.probe(N, a, a + rows)), tri(i0 + rows) - tri(i0))
+            for i0 in range(N // 2, N, rows)]
+
+
+def cpu_oracle_sample(seconds_target=6.0):
+    """The oracle probe on one core and on all cores, ~seconds_target each."""
+    return cpu_baseline_entry(probe_items(), seconds_target, UNIT,
+                              "whole rows of the N=65536 triangle from row 32768 on, 256 rows per work item")
 
 
 def run_reference(args):
@@ -159,26 +205,25 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle  # noqa: F401  (builds/loads the C oracle before timing)
-    N = 65536
-    rows = 512  # one step: 512 whole rows from the middle of the N = 65536 triangle
-    def step(k):
-        i0 = (N // 2 + k * rows) % (N - rows)
-        oracle.probe(N, i0, i0 + rows)
-        return tri(i0 + rows) - tri(i0)
-    for k in range(args.warmup):
-        step(k)
-    pairs, t0 = 0, time.perf_counter()
-    for k in range(args.steps):
-        pairs += step(args.warmup + k)
-    dt = time.perf_counter() - t0
+    items = probe_items(rows=64)
+    cores = host_cores()
+    seconds = 1.0  # one step: about a second of all-core oracle work on whole rows of the triangle
+    for _ in range(args.warmup):
+        cpu_rate(items, 0.2, cores)
+    pairs, dt = 0, 0.0
+    for _ in range(args.steps):
+        _, u, t = cpu_rate(items, seconds, cores)
+        pairs += u
+        dt += t
     v = pairs / dt
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (no input; hash of (i, j))",
         "config": headline_config(args.sched),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{rows} whole rows of the N=65536 triangle per step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "per step, about 1 s of whole rows (64 at a time) of the N=65536 triangle from "
+                                   "row 32768 on, threads over disjoint rows"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -359,9 +404,11 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        v, pairs, dt = cpu_oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{pairs} pairs: whole rows of the N=65536 triangle from row 32768 on, {dt:.1f} s"}
+        cpu = cpu_oracle_sample()
+
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = run_configs(args, td, stream)
 
     if rank == 0:
         print(json.dumps({
@@ -375,9 +422,247 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "compare": compare,
+            "configs": configs,
         }), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def load_peak_table():
+    """MEASURED_PEAKS.json as written on the box (copy GB/s, BF16 TF/s burst and sustained, SM clock)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+            "fallback"
+
+
+def alu_peak_ops(torch):
+    """FP32 / INT32 issue peak: SMs x 128 lanes x the maximum SM clock (an FMA counts once)."""
+    table, _ = load_peak_table()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = float(table.get("sm_max_mhz", 2070.0))
+    return sms * 128 * mhz * 1e6, f"{sms} SMs x 128 lanes x {mhz:.0f} MHz"
+
+
+def _events_ms(torch, stream, fn, reps, warmup=3):
+    """Mean device time of fn() over `reps` back-to-back calls, CUDA events on `stream`."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _rel_err(got, want):
+    import numpy as np
+    got = np.asarray(got, dtype=np.float64)
+    rel = np.abs(got - want) / np.maximum(want, 1e-30)
+    rel[want == 0] = np.abs(got[want == 0])
+    return {"max_rel": float(rel.max()), "rms_rel": float(np.sqrt((rel ** 2).mean())), "pairs": int(want.size)}
+
+
+def run_configs(args, td, stream):
+    """The other workloads of the method, each timed by CUDA events in this run, with its roofline,
+    a sampled check against the oracle and the oracle's own throughput on the host cores:
+    plain EDM (n = 2048, d = 3, and n = 8192, 32768), the collision table (n = 32768), the precision
+    form (BF16 Gram vs FP32 direct, n = 16384, d = 256) and the batched form (512 problems)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_1308_1419_gb300 import synth
+
+    peaks, peak_kind = load_peak_table()
+    copy = float(peaks["hbm_gbs"])
+    alu, alu_how = alu_peak_ops(torch)
+    cpu_s = 1.0 if not args.no_cpu else 0.0
+    configs = {}
+
+    def cpu_entry(items, sample):
+        return cpu_baseline_entry(items, cpu_s, UNIT, sample) if cpu_s > 0 else None
+
+    # ---- 1. plain EDM: n = 2048, d = 3, rho = 16 (launch-bound: the 8.4 MB output sits in L2), then
+    # the store-bound sizes n = 8192 and 32768 (outputs of 134 MB and 2.1 GB, beyond L2)
+    xh = synth.plain_edm()
+    x = torch.from_numpy(xh).cuda()
+    n = xh.shape[0]
+    out = torch.empty(tri(32768), dtype=torch.float32, device="cuda")
+    ms = {}
+    for strat in ("LTM", "BB"):
+        for sched in ("grid", "persistent", "chunked"):
+            ms[f"{strat}/{sched}"] = _graph_ms(lambda: td.td_edm(strat, sched, x, 16, out), 20)
+    best = min((k for k in ms if k.startswith("LTM/")), key=ms.get)
+    got, _ = td.td_edm(best.split("/")[0], best.split("/")[1], x, 16, out)
+    err = _rel_err(got[: tri(n)].cpu().numpy(), oracle.edm(xh))
+    sweep = {}
+    for nn in (8192, 32768):
+        xs = torch.from_numpy(synth.uniform_points(nn, 3, synth.seed_for(1))).cuda()
+        row = {}
+        for strat in ("LTM", "BB"):
+            row[f"{strat}/chunked/16"] = _events_ms(torch, stream, lambda: td.td_edm(strat, "chunked", xs, 16, out), 10)
+            row[f"{strat}/persistent/128"] = _events_ms(
+                torch, stream, lambda: td.td_edm(strat, "persistent", xs, 128, out), 10)
+        ltm_best = min((k for k in row if k.startswith("LTM/")), key=row.get)
+        bb_best = min((k for k in row if k.startswith("BB/")), key=row.get)
+        gbps = 4 * tri(nn) / (row[ltm_best] / 1e3) / 1e9
+        sweep[str(nn)] = {"ms": row, "best_LTM": ltm_best, "pairs_per_s": tri(nn) / (row[ltm_best] / 1e3),
+                          "I_best_BB_over_best_LTM": row[bb_best] / row[ltm_best],
+                          "roofline": {"bound": "hbm", "achieved": gbps, "peak": copy, "unit": "GB/s",
+                                       "frac": gbps / copy}}
+    rows = 64
+    configs["plain_edm"] = {
+        "workload": "EDM n=2048, d=3, x ~ U[0,1)^3 (seed 1309), rho=16; each schedule replayed 20x in a CUDA graph "
+                    "(output 8.4 MB, L2-resident: launch-bound); store-bound sizes n=8192, 32768 below",
+        "pairs": tri(n), "ms": ms, "best_LTM": best, "pairs_per_s": tri(n) / (ms[best] / 1e3),
+        "I_vs_BB_same_schedule": {sc: ms[f"BB/{sc}"] / ms[f"LTM/{sc}"] for sc in ("grid", "persistent", "chunked")},
+        "roofline": {"bound": "hbm", "achieved": 4 * tri(n) / (ms[best] / 1e3) / 1e9, "peak": copy, "unit": "GB/s",
+                     "frac": 4 * tri(n) / (ms[best] / 1e3) / 1e9 / copy,
+                     "note": "L2-resident output; the n=32768 entry of 'sweep' is the HBM roofline case"},
+        "error_vs_fp64_oracle": err, "tolerance": 2e-6,
+        "sweep": sweep,
+        "cpu_baseline": cpu_entry([((lambda a=i0: oracle.edm(xh, a, min(a + rows, n))),
+                                    tri(min(i0 + rows, n)) - tri(i0)) for i0 in range(0, n, rows)],
+                                  "the FP64 oracle distance map of this n=2048 input, 64 whole rows per work item"),
+    }
+
+    # ---- 3. collision table: n = 32768 spheres (FP32/INT32 issue-bound: 9 operations per pair)
+    c, r = synth.spheres()
+    ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+    nc = r.size
+    table = torch.empty(td.td_collide_words(nc), dtype=torch.int32, device="cuda")
+    cms = {}
+    for strat in ("LTM", "BB"):
+        for sched in ("grid", "persistent"):
+            cms[f"{strat}/{sched}"] = _events_ms(torch, stream, lambda: td.td_collide(strat, sched, ct, rt, table), 20)
+    cbest = min((k for k in cms if k.startswith("LTM/")), key=cms.get)
+    td.td_collide(cbest.split("/")[0], cbest.split("/")[1], ct, rt, table)
+    rng = np.random.default_rng(7)
+    ii = rng.integers(1, nc, 200000).astype(np.uint32)
+    jj = (rng.random(ii.size) * ii).astype(np.uint32)
+    words = table.cpu().numpy().view(np.uint32)
+    bi, bj = ii.astype(np.int64) // 32, jj.astype(np.int64) // 32
+    w = 32 * (bi * (bi + 1) // 2 + bj) + ii % 32
+    gbits = (words[w] >> (jj % 32).astype(np.uint32)) & 1
+    pairs_c = nc * (nc - 1) // 2
+    ops = 9 * pairs_c / (cms[cbest] / 1e3)
+    groups = [(np.ascontiguousarray(c[g:g + 2048]), np.ascontiguousarray(r[g:g + 2048])) for g in range(0, nc, 2048)]
+    configs["collision"] = {
+        "workload": "collision table n=32768, centres int32 U[0,2^20)^3, radii U[256,2048] (seed 1311), 32x32 bit tiles",
+        "pairs": pairs_c, "ms": cms, "best_LTM": cbest, "pairs_per_s": pairs_c / (cms[cbest] / 1e3),
+        "I_vs_BB_same_schedule": {sc: cms[f"BB/{sc}"] / cms[f"LTM/{sc}"] for sc in ("grid", "persistent")},
+        "roofline": {"bound": "alu", "achieved": ops, "peak": alu, "unit": "op/s", "frac": ops / alu,
+                     "ops_per_pair": 9, "peak_how": alu_how},
+        "sampled_pairs_bit_exact": bool(np.array_equal(gbits.astype(np.uint8), oracle.collide_pairs(c, r, ii, jj))),
+        "sampled_pairs": int(ii.size),
+        "cpu_baseline": cpu_entry([((lambda g=g: oracle.collide(g[0], g[1])), tri(2047)) for g in groups],
+                                  "the 128-bit oracle table of 2048-sphere groups of this input, one group per "
+                                  "work item"),
+    }
+    del table
+
+    # ---- 4. precision form: BF16 Gram on tcgen05 + FP32 recompute, against the FP32 direct kernel
+    xp_h = synth.clustered_points()
+    np_, dp = xp_h.shape
+    xp = torch.from_numpy(xp_h).cuda()
+    outp = torch.empty(tri(np_), dtype=torch.float32, device="cuda")
+    wsg = torch.empty(td.td_edm_gram_workspace(np_, dp) + 1024, dtype=torch.uint8, device="cuda")
+    t_gram = _events_ms(torch, stream, lambda: td.td_edm_gram(xp, outp, wsg), 10)
+    fallback = td.td_edm_gram_status(wsg)
+    ii = rng.integers(0, np_, 20000).astype(np.uint32)
+    jj = (rng.random(ii.size) * (ii.astype(np.float64) + 1)).astype(np.uint32)
+    pos = torch.from_numpy(ii.astype(np.int64) * (ii.astype(np.int64) + 1) // 2 + jj).cuda()
+    want = oracle.edm_pairs(xp_h, ii, jj)
+    gram_err = _rel_err(outp[pos].cpu().numpy(), want)
+    t_direct = _events_ms(torch, stream, lambda: td.td_edm("LTM", "persistent", xp, 128, outp), 5)
+    direct_err = _rel_err(outp[pos].cpu().numpy(), want)
+    gbps = 4 * tri(np_) / (t_gram / 1e3) / 1e9
+    tflops = 2 * dp * tri(np_) / (t_gram / 1e3) / 1e12
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    chunks = [(ii[k:k + 4096], jj[k:k + 4096]) for k in range(0, ii.size, 4096)]
+    configs["precision"] = {
+        "workload": "EDM n=16384, d=256, 64 Gaussian clusters (sigma 0.05, seed 1312); BF16 Gram on tcgen05 with "
+                    "FP32 accumulate + FP32 direct recompute where D^2 < 1e-2 (|x|^2 + |y|^2)",
+        "pairs": tri(np_), "ms": {"gram_bf16": t_gram, "direct_fp32_LTM_rho128": t_direct},
+        "pairs_per_s": tri(np_) / (t_gram / 1e3), "speedup_vs_direct_fp32": t_direct / t_gram,
+        "recomputed_pairs": fallback, "recomputed_fraction": fallback / tri(np_),
+        "error_vs_fp64_oracle": {"gram": gram_err, "direct_fp32": direct_err},
+        "roofline": {"bound": "hbm", "achieved": gbps, "peak": copy, "unit": "GB/s", "frac": gbps / copy,
+                     "note": "output bytes of the whole form (main pass + recompute) over its time"},
+        "tensor": {"achieved_tflops": tflops, "peak_tflops": bf16, "frac": tflops / bf16,
+                   "flops": "2 d per pair of the triangle"},
+        "direct_alu": {"achieved": 2 * dp * tri(np_) / (t_direct / 1e3), "peak": alu,
+                       "frac": 2 * dp * tri(np_) / (t_direct / 1e3) / alu, "unit": "op/s"},
+        "cpu_baseline": cpu_entry([((lambda a=a, b=b: oracle.edm_pairs(xp_h, a, b)), a.size) for a, b in chunks],
+                                  "the FP64 oracle distance of 4096 random pairs of this input per work item"),
+    }
+    del outp, wsg
+
+    # ---- 5. batched form: 512 problems in one persistent launch, against one launch per problem
+    ns, ds, xb_h = synth.batched_problems()
+    xb = torch.from_numpy(xb_h).cuda()
+    xs_, os_ = td.batched_sizes(ns, ds)
+    outb = torch.empty(os_, dtype=torch.float32, device="cuda")
+    wsb = torch.empty(td.td_edm_batched_workspace(len(ns)), dtype=torch.uint8, device="cuda")
+    (rho_t, cps_t), tune_ms = td.td_edm_batched_autotune(ns, ds, xb, outb, wsb)
+    total = td.td_edm_batched_plan(ns, ds, rho_t, wsb)
+    bms = {"one_launch": _events_ms(torch, stream,
+                                    lambda: td.td_edm_batched_run(len(ns), rho_t, total, xb, outb, wsb, cps_t), 5)}
+    bms["one_launch_graph"] = _graph_ms(lambda: td.td_edm_batched_run(len(ns), rho_t, total, xb, outb, wsb, cps_t), 5)
+    xo, oo = [0], [0]
+    for nq, dq in zip(ns, ds):
+        xo.append(xo[-1] + int(nq) * int(dq))
+        oo.append(oo[-1] + tri(int(nq)))
+    # per-problem buffers of their own: td_edm wants 16-byte-aligned points and output
+    xs_l = [xb[xo[p]: xo[p + 1]].view(int(ns[p]), int(ds[p])).clone() for p in range(len(ns))]
+    outs_l = [torch.empty(oo[p + 1] - oo[p], dtype=torch.float32, device="cuda") for p in range(len(ns))]
+
+    def per_problem():
+        for p in range(len(ns)):
+            td.td_edm("LTM", "persistent", xs_l[p], 128, outs_l[p])
+    bms["per_problem"] = _events_ms(torch, stream, per_problem, 3, warmup=1)
+    bms["per_problem_graph"] = _graph_ms(per_problem, 3)
+    td.td_edm_batched_run(len(ns), rho_t, total, xb, outb, wsb, cps_t)
+    torch.cuda.synchronize()
+    order = np.argsort(ns, kind="stable")
+    check = list(order[:4]) + [p for p in order if ds[p] == 64 and 1000 < ns[p] < 2000][:2]
+    errs = [_rel_err(outb[oo[p]: oo[p + 1]].cpu().numpy(),
+                     oracle.edm(xb_h[xo[p]: xo[p + 1]].reshape(int(ns[p]), int(ds[p])))) for p in check]
+    ops_b = sum(2 * int(dq) * tri(int(nq)) for nq, dq in zip(ns, ds))
+    tb = bms["one_launch"]
+    items = []
+    for p in range(len(ns)):
+        nq, dq = int(ns[p]), int(ds[p])
+        step = max(1, (1 << 18) // max(nq, 1))
+        xq = xb_h[xo[p]: xo[p + 1]].reshape(nq, dq)
+        for i0 in range(0, nq, step):
+            i1 = min(i0 + step, nq)
+            items.append(((lambda xq=xq, a=i0, b=i1: oracle.edm(xq, a, b)), tri(i1) - tri(i0)))
+    perm = np.random.default_rng(1313).permutation(len(items))
+    configs["batched"] = {
+        "workload": "512 EDM problems, n = floor(64 * 128^U) in [64, 8192], d from {3, 16, 64}, x ~ U[0,1) "
+                    "(seed 1313); one persistent launch (prefix-sum search, then g) vs one td_edm launch per problem",
+        "pairs": os_, "autotuned": {"rho": rho_t, "ctas_per_sm": cps_t, "ms": tune_ms}, "ms": bms,
+        "pairs_per_s": os_ / (tb / 1e3),
+        "speedup_vs_per_problem": bms["per_problem"] / tb,
+        "speedup_vs_per_problem_graph": bms["per_problem_graph"] / tb,
+        "roofline": {"bound": "alu", "achieved": ops_b / (tb / 1e3), "peak": alu, "unit": "op/s",
+                     "frac": ops_b / (tb / 1e3) / alu, "ops": "2 d_p FP32 instructions per pair", "peak_how": alu_how},
+        "error_vs_fp64_oracle": {"problems_checked": [int(p) for p in check],
+                                 "max_rel": max(e["max_rel"] for e in errs)},
+        "cpu_baseline": cpu_entry([items[k] for k in perm],
+                                  "the FP64 oracle distance map over row ranges (~2^18 pairs each) of the batch's "
+                                  "problems, in a seeded random order so that any prefix mixes the three d"),
+    }
+    configs["peaks"] = {"copy_GBps": copy, "bf16_tflops": float(peaks.get("bf16_tflops", 0.0)), "alu_ops": alu,
+                        "kind": peak_kind}
+    return configs
 
 
 def run_case(args):
@@ -580,14 +865,15 @@ def _graph_ms(fn, steps):
 
 def run_ltm_variant_sweep(args):
     """The LTM implementation comparison of Sec. III-A: the map-only dummy kernel, and the probe
-    body, under BB and under each evaluation of g (exact fix-up, LTM-X, LTM-N, LTM-R),
+    body, under BB and under each evaluation of g (exact fix-up, LTM-X, LTM-N rounded per
+    operation and contracted into fused multiply-adds, LTM-R),
     N = 1024 k (k = 1 .. 30), rho = 16, paper-style GRID launch; I = t_BB / t_variant.  Also each
     variant's first failing lambda below 2^32 (the exact g has none)."""
     import torch
     from paper_1308_1419_gb300 import td
 
     sizes = [1024 * k for k in range(1, 31)]
-    maps = ["BB", "LTM", "LTM-X", "LTM-N", "LTM-R"]
+    maps = ["BB", "LTM", "LTM-X", "LTM-N", "LTM-N-FMA", "LTM-R"]
     sched = args.sched if args.sched != "chunked" else "grid"
     steps = max(3, min(10, args.steps))
     sink = torch.zeros(4, dtype=torch.int32, device="cuda")
@@ -617,6 +903,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-compare", action="store_true", help="skip the BB/UTM/RB/REC comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (plain EDM, collision, precision, batched)")
     ap.add_argument("--sched", default="chunked", choices=["chunked", "persistent", "grid"],
                     help="schedule of the headline g(lambda) sweep")
     ap.add_argument("--sweep", default=None, choices=["edm-features", "ltm-variants"],

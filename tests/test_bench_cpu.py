@@ -27,3 +27,22 @@ def test_reference_arm_prints_contract_line():
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0 and line["config"] == bench.headline_config("chunked")
+
+
+def test_cpu_rate_counts_every_item_it_ran():
+    """The host-core timer of the oracle baselines: each thread takes whole work items, and the
+    units reported are the sum of the items that ran, over the wall time of all threads."""
+    import threading
+    ran, lock = [], threading.Lock()
+
+    def item(k):
+        def fn():
+            with lock:
+                ran.append(k)
+        return fn, k + 1
+
+    v, units, dt = bench.cpu_rate([item(k) for k in range(5)], 0.05, 3)
+    assert units == sum(k + 1 for k in ran) and units > 0 and dt >= 0.05 and v == units / dt
+    e = bench.cpu_baseline_entry(bench.probe_items(rows=64)[:4], 0.05, "pairs/s", "sample")
+    assert e["cores"] == bench.host_cores() and e["all_cores"]["cores"] == e["cores"]
+    assert e["one_core"]["cores"] == 1 and e["value"] == e["all_cores"]["value"] > 0
