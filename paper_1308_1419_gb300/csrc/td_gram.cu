@@ -21,9 +21,10 @@
 //                            shared-memory atomic per warp and 32 columns), take the square root
 //                            and write packed rows through a per-warp transpose in shared memory.
 //                The two accumulators let the next block's loads and MMAs run under the epilogue.
-//   k_gram_fix   recomputes the queued pairs in the direct form: one warp per 2 pairs, 16-byte loads,
-//                lanes striding the features, partial sums combined in a fixed butterfly order; 32
-//                warps per queue segment.
+//   k_gram_fix   recomputes the queued pairs in the direct form: one pair per 8-lane group, 16-byte
+//                loads (a whole 128-byte line of each point per group load), lanes striding the
+//                features, partial sums combined in a fixed butterfly order; 32 warps per queue
+//                segment.
 // If a segment is full, the epilogue recomputes the extra pairs itself.  Every mbarrier wait is
 // bounded; a timeout records an error code in the workspace status word and the roles wind down,
 // the tensor memory is released and the CTA ends.
@@ -320,59 +321,52 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// Direct FP32 recompute of the queued pairs: FIX_WARPS warps per queue segment, a warp takes
-// FIX_PAIRS pairs at a time, lanes stride the features 4 at a time (16-byte loads, two iterations
-// in flight), and the per-lane partial sums are combined in a fixed butterfly order.  d is a
-// multiple of 4.  Launched with gsize * FIX_WARPS / 8 CTAs of 256 threads.  (Walking all segments
-// as one list balances better but ran 1.7x slower on the clustered workload: every warp then
-// works in the same few blocks at once.)
-constexpr int FIX_PAIRS = 2;
+// Direct FP32 recompute of the queued pairs: FIX_WARPS warps per queue segment, each warp in
+// groups of FIX_LPP lanes, one pair per group (FIX_PPW pairs per warp step).  Lane r of a group
+// reads float4 r, r + FIX_LPP, ... of both points, so each load of the group covers one whole
+// 128-byte line of each point; its partial sums are combined in a fixed butterfly order within
+// the group.  d is a multiple of 4.  Launched with gsize * FIX_WARPS / 8 CTAs of 256 threads.
+// (A whole warp per pair spent a 5-level butterfly per pair and ran about 4x the instructions;
+// walking all segments as one list balances better but ran 1.7x slower on the clustered
+// workload: every warp then works in the same few blocks at once.)
 constexpr uint32_t FIX_WARPS = 32;
+constexpr uint32_t FIX_LPP = 8;
+constexpr uint32_t FIX_PPW = 32 / FIX_LPP;
 
 __global__ void __launch_bounds__(256, 4) k_gram_fix(const float *__restrict__ x, uint32_t d,
                                                      const uint2 *__restrict__ queue,
                                                      const uint32_t *__restrict__ seg_count, uint32_t seg,
                                                      uint32_t gsize, float *__restrict__ out)
 {
-    const uint32_t lane = threadIdx.x & 31, d4 = d / 4;
+    const uint32_t lane = threadIdx.x & 31, d4 = d / 4, grp = lane / FIX_LPP, sub = lane % FIX_LPP;
     const uint32_t wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint32_t c = wid % gsize, kw = wid / gsize;  // segment, and this warp's rank in it
     if (kw >= FIX_WARPS) return;
     const uint32_t cnt = seg_count[c];
     const uint64_t total = cnt < seg ? cnt : seg;
     const uint2 *qs = queue + uint64_t(c) * seg;
-    for (uint64_t e = uint64_t(kw) * FIX_PAIRS; e < total; e += FIX_WARPS * FIX_PAIRS) {
-        const float4 *xi[FIX_PAIRS], *xj[FIX_PAIRS];
-        uint2 pr[FIX_PAIRS];
-        float part[FIX_PAIRS];
-#pragma unroll
-        for (int p = 0; p < FIX_PAIRS; ++p) {
-            pr[p] = e + p < total ? qs[e + p] : make_uint2(0u, 0u);
-            xi[p] = reinterpret_cast<const float4 *>(x + uint64_t(pr[p].x) * d);
-            xj[p] = reinterpret_cast<const float4 *>(x + uint64_t(pr[p].y) * d);
-            part[p] = 0.0f;
-        }
-#pragma unroll 2
-        for (uint32_t k4 = lane; k4 < d4; k4 += 32) {
-#pragma unroll
-            for (int p = 0; p < FIX_PAIRS; ++p) {
-                const float4 a = __ldg(xi[p] + k4), b = __ldg(xj[p] + k4);
-                float t = a.x - b.x;
-                part[p] = fmaf(t, t, part[p]);
-                t = a.y - b.y;
-                part[p] = fmaf(t, t, part[p]);
-                t = a.z - b.z;
-                part[p] = fmaf(t, t, part[p]);
-                t = a.w - b.w;
-                part[p] = fmaf(t, t, part[p]);
-            }
+    for (uint64_t e0 = uint64_t(kw) * FIX_PPW; e0 < total; e0 += FIX_WARPS * FIX_PPW) {  // warp-uniform
+        const uint64_t e = e0 + grp;
+        const bool live = e < total;
+        const uint2 pr = live ? qs[e] : make_uint2(0u, 0u);
+        const float4 *xi = reinterpret_cast<const float4 *>(x + uint64_t(pr.x) * d);
+        const float4 *xj = reinterpret_cast<const float4 *>(x + uint64_t(pr.y) * d);
+        float part = 0.0f;
+#pragma unroll 4
+        for (uint32_t k4 = sub; k4 < d4; k4 += FIX_LPP) {
+            const float4 a = __ldg(xi + k4), b = __ldg(xj + k4);
+            float t = a.x - b.x;
+            part = fmaf(t, t, part);
+            t = a.y - b.y;
+            part = fmaf(t, t, part);
+            t = a.z - b.z;
+            part = fmaf(t, t, part);
+            t = a.w - b.w;
+            part = fmaf(t, t, part);
         }
 #pragma unroll
-        for (int p = 0; p < FIX_PAIRS; ++p) {
-            float s2 = part[p];
-            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            if (lane == 0 && e + p < total) out[tri(pr[p].x) + pr[p].y] = dist_sqrt(s2);
-        }
+        for (uint32_t o = FIX_LPP / 2; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (live && sub == 0) out[tri(pr.x) + pr.y] = dist_sqrt(part);
     }
 }
 
