@@ -742,11 +742,13 @@ def run_case(args):
         def call():
             td.td_edm_gram(x, out, ws)
     elif kind == "batched":
-        # batched:<how>:<rho>:<ctas_per_sm>, how = one (single persistent launch), graph (its graph
-        # replay), per (one td_edm launch per problem), pergraph (those launches as one graph),
-        # tune (autotuned one launch)
+        # batched:<how>:<rho>:<ctas_per_sm>[:<nprob>], how = one (single persistent launch), graph (its
+        # graph replay), per (one td_edm launch per problem), pergraph (those launches as one graph),
+        # tune (autotuned one launch); nprob: the first problems of the 512-problem batch's recipe
+        # (default all 512)
         how, rho, cps = strategy, int(sched), int(parts[3])
-        ns, ds, xh = synth.batched_problems()
+        nprob = int(parts[4]) if len(parts) > 4 else 512
+        ns, ds, xh = synth.batched_problems(nprob=nprob)
         x = torch.from_numpy(xh).cuda()
         xs, os_ = td.batched_sizes(ns, ds)
         out = torch.empty(os_, dtype=torch.float32, device="cuda")
