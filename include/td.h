@@ -161,9 +161,10 @@ td_status td_map_probe(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho
 
 /* Euclidean distance map (Sec. IV): for every 0 <= j <= i < n,
  *     out[T(i) + j] = sqrt(sum_{k<d} (x[i][k] - x[j][k])^2)     in FP32,
- * evaluated as t = x[i][k] - x[j][k], s = fma(t, t, s) for k = 0 .. d-1 from s = 0, then a
- * correctly rounded sqrt -- the same order in every kernel, so every strategy, schedule and
- * rho gives bit-identical output.  x: device, float[n][d] row-major, 16-byte aligned;
+ * evaluated as t = x[i][k] - x[j][k], s = fma(t, t, s) for k = 0 .. d-1 from s = 0, then the
+ * hardware square root sqrt.approx.f32 (within 2 units in the last place of the correctly
+ * rounded one) -- the same order and square root in every kernel, so every strategy, schedule
+ * and rho gives bit-identical output.  x: device, float[n][d] row-major, 16-byte aligned;
  * out: device, float[T(n)], 16-byte aligned.  d >= 1.
  * rho in {8, 16, 32}, sched GRID or PERSISTENT: rho x rho threads per block, one element per
  *   thread, every strategy (the paper's EDM kernel).

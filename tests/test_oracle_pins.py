@@ -232,6 +232,29 @@ def test_strategy_bijection_sizes(strategy, N, rho):
     assert np.all(count == 1)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("strategy", ["UTM", "RB", "REC"])
+def test_strategy_bijection_every_side_to_4096(strategy):
+    """UTM, RB and REC depend on the triangle's side, so each is walked for every side N = 1 .. 4096
+    (about 1.15e10 mapped elements per strategy) at the element level (rho = 1: REC then splits
+    N = m 2^k with m odd), and every element of the triangle must be reached exactly once.
+    Block-level UTM is the same formula applied to the block triangle of side nb, so the UTM walk
+    covers it for every nb <= 4096; g(lambda) does not depend on the side at all (walked over
+    every lambda < T(4096) above).  The sides are spread over the host's cores; each call into
+    the C walk runs with the interpreter lock released."""
+    import concurrent.futures as cf
+    import os
+
+    def check(N):
+        count, st = oracle.cover(strategy, N, 1)
+        return N, bool(count.min() == 1 and count.max() == 1 and st["hits"] == N * (N + 1) // 2)
+
+    sides = range(4096, 0, -1)  # largest first, so the threads finish together
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        bad = [N for N, ok in ex.map(check, sides) if not ok]
+    assert not bad, (strategy, bad[:10])
+
+
 def test_rec_levels_and_launch_count():
     # N = m 2^k with m a multiple of rho and k as large as possible (Sec. III-B)
     assert oracle.rec_levels(1024, 16) == (6, 16)
