@@ -147,6 +147,34 @@ td_status td_plan(td_mapping m, td_schedule sched, uint32_t N, uint32_t rho, td_
 td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_t *br0, uint32_t *br1, uint64_t *off0,
                        uint64_t *off1);
 
+/* Slices of whole block rows, the units of a partition over several GPUs (td_partition).  Block
+ * rows [br0, br1) of a triangle of side N with block side rho hold the g(lambda) blocks
+ * lambda in [T(br0), T(br1)) (Sec. II-A, Eq. (matrix_indexing): block rows are contiguous in
+ * lambda) and, in the packed output, the contiguous elements [e0, e1) with
+ * e0 = T(min(br0 rho, N)), e1 = T(min(br1 rho, N)).  Each call below computes only its slice: it
+ * issues the slice's blocks (m = TD_MAP_LTM: lambda in [T(br0), T(br1)); TD_MAP_BB: the bounding
+ * box rows br0 .. br1 - 1) and writes out[e - e0] for every element e of the slice, exactly the
+ * values the whole-triangle call writes there -- so slices [b_0, b_1), [b_1, b_2), ... written one
+ * after another into consecutive buffers reproduce the whole packed output byte for byte.
+ * rho is a multiple of 8, so e0 and (unless e1 = T(N)) e1 are multiples of 4 and the chunked
+ * kernels' aligned 16-byte chunks never straddle two slices.  0 <= br0 < br1 <= ceil(N / rho),
+ * else TD_ERR_INVALID_ARG; other mappings: TD_ERR_UNSUPPORTED.  out: device, e1 - e0 elements,
+ * 16-byte aligned.  stats (host, may be NULL): the slice's blocks.  Asynchronous on `stream`.
+ *
+ * td_map_probe_rows: the probe of td_map_probe under TD_SCHED_CHUNKED; rho in {8, 16, 32}.
+ * td_edm_rows: the distance map of td_edm (same summation order, bit-identical values) under
+ *   TD_SCHED_CHUNKED with rho in {8, 16, 32} and d <= 8, or under TD_SCHED_GRID / PERSISTENT with
+ *   rho in {64, 128} (the register-tiled body); x as in td_edm (all n points).
+ * td_collide_rows: the collision table of td_collide over tile rows [tr0, tr1) of the tile
+ *   triangle of side ceil(n / 32): the words [32 T(tr0), 32 T(tr1)) of the whole table, written
+ *   to table[w - 32 T(tr0)]; sched GRID or PERSISTENT. */
+td_status td_map_probe_rows(td_mapping m, uint32_t N, uint32_t rho, uint32_t br0, uint32_t br1, uint32_t *out,
+                            td_launch_stats *stats, void *stream);
+td_status td_edm_rows(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho,
+                      uint32_t br0, uint32_t br1, float *out, td_launch_stats *stats, void *stream);
+td_status td_collide_rows(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
+                          uint32_t tr0, uint32_t tr1, uint32_t *table, td_launch_stats *stats, void *stream);
+
 /* ------------------------------------------------------------------ mapping kernels */
 
 /* Probe: the paper's dummy kernel (Sec. III-A, Sec. IV test (1)) made to write the whole

@@ -167,6 +167,25 @@ td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, P
     return TD_OK;
 }
 
+td_status plan_rows(td_mapping m, uint32_t br0, uint32_t br1, Plan &p)
+{
+    if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "block-row slices serve LTM and BB");
+    if (br0 >= br1 || br1 > p.nb)
+        return fail(TD_ERR_INVALID_ARG, "block rows [%u, %u) must satisfy br0 < br1 <= %u", br0, br1, p.nb);
+    const uint64_t useful = tri(br1) - tri(br0);
+    p.sliced = true;
+    if (m == TD_MAP_LTM) {
+        p.slice_u0 = tri(br0);
+        p.slice_units = useful;
+    } else {
+        p.slice_u0 = uint64_t(br0) * p.nb;
+        p.slice_units = uint64_t(br1 - br0) * p.nb;
+    }
+    p.blocks = p.slice_units;
+    p.useful = useful;
+    return TD_OK;
+}
+
 static int g_options[TD_OPT_COUNT] = {0};
 
 int option(td_option opt) { return (opt >= 0 && opt < TD_OPT_COUNT) ? g_options[opt] : 0; }
@@ -189,6 +208,24 @@ static td_status plan_strict_blocks(td_mapping m, uint32_t n, uint32_t rho, Plan
     if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "the block-mapped strict forms serve LTM and BB");
     if (rho != 8 && rho != 16 && rho != 32) return fail(TD_ERR_INVALID_ARG, "the block-mapped strict forms need rho 8, 16 or 32 (got %u)", rho);
     return plan_strategy(m, TD_SCHED_CHUNKED, n < 2 ? 0 : n - 1, rho, p);
+}
+
+// Packed offset of the first element of block row b: T(min(b rho, N)).  For rho a multiple of 8 it
+// is a multiple of 4 (T(8k) = 4k (8k + 1)), so a slice of whole block rows starts and (unless it
+// ends at T(N)) ends on the 16-byte grid of the whole packed array: the aligned chunks of the
+// chunked kernels never cross a slice boundary, and the slice is the whole-triangle kernel
+// restricted to the slice's blocks, writing through a base pointer moved back by this offset
+// (integer arithmetic on the address; only addresses inside the slice are formed in the kernel).
+uint64_t row_offset(uint32_t b, uint32_t rho, uint32_t N)
+{
+    const uint64_t r = uint64_t(b) * rho;
+    return tri(r < N ? r : N);
+}
+
+template <class T>
+T *slice_base(T *out, uint64_t e0)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<uintptr_t>(out) - e0 * sizeof(T));
 }
 
 }  // namespace td
@@ -342,7 +379,7 @@ td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, co
     if (sched == TD_SCHED_GRID && (p.blocks + 7) / 8 > kMaxGridX)
         return fail(TD_ERR_UNSUPPORTED, "grid launch too large; use the persistent schedule");
     uint64_t ctas = 0;
-    const td_status st = launch_collide(m, sched, centers, radii, n, table, static_cast<cudaStream_t>(stream), &ctas);
+    const td_status st = launch_collide(m, sched, centers, radii, n, table, p, static_cast<cudaStream_t>(stream), &ctas);
     fill_stats(stats, p, ctas);
     return st;
 }
@@ -456,6 +493,74 @@ td_status td_wait_selftest(uint32_t arrive, uint64_t limit_ns, uint64_t *ws, uin
     if (waited_ns) *waited_ns = rec[1];
     if (rec[0] != 0) return fail(TD_ERR_TIMEOUT, "td_wait_selftest: the wait ran out after %llu ns", (unsigned long long)rec[1]);
     return TD_OK;
+}
+
+td_status td_map_probe_rows(td_mapping m, uint32_t N, uint32_t rho, uint32_t br0, uint32_t br1, uint32_t *out,
+                            td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    if (rho != 8 && rho != 16 && rho != 32) return fail(TD_ERR_INVALID_ARG, "the probe needs rho 8, 16 or 32 (got %u)", rho);
+    Plan p;
+    td_status st = plan_strategy(m, TD_SCHED_CHUNKED, N, rho, p);
+    if (st != TD_OK) return st;
+    st = plan_rows(m, br0, br1, p);
+    if (st != TD_OK) return st;
+    if (!out) return fail(TD_ERR_INVALID_ARG, "output pointer is NULL");
+    if (!aligned16(out)) return fail(TD_ERR_INVALID_ARG, "output pointer must be 16-byte aligned");
+    uint64_t ctas = 0;
+    st = launch_probe(m, TD_SCHED_CHUNKED, N, rho, slice_base(out, row_offset(br0, rho, N)), false, p,
+                      static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
+}
+
+td_status td_edm_rows(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho,
+                      uint32_t br0, uint32_t br1, float *out, td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    const bool chunked = sched == TD_SCHED_CHUNKED;
+    if (chunked ? (rho != 8 && rho != 16 && rho != 32) : (rho != 64 && rho != 128))
+        return fail(TD_ERR_UNSUPPORTED, "td_edm_rows: rho 8, 16 or 32 under CHUNKED, 64 or 128 under GRID/PERSISTENT");
+    if (d == 0) return fail(TD_ERR_INVALID_ARG, "d must be at least 1");
+    Plan p;
+    td_status st = plan_strategy(m, sched, n, rho, p);
+    if (st != TD_OK) return st;
+    st = plan_rows(m, br0, br1, p);
+    if (st != TD_OK) return st;
+    if (!x || !out) return fail(TD_ERR_INVALID_ARG, "x and out must be non-NULL");
+    if (!aligned16(x) || !aligned16(out)) return fail(TD_ERR_INVALID_ARG, "x and out must be 16-byte aligned");
+    float *base = slice_base(out, row_offset(br0, rho, n));
+    const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    uint64_t ctas = 0;
+    st = chunked ? launch_edm_chunked(m, x, n, d, rho, base, p, false, cs, &ctas)
+                 : launch_edm_tiled(m, sched, x, n, d, rho, base, p, option(TD_OPT_EDM_F32X2) != 0, cs, &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
+}
+
+td_status td_collide_rows(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
+                          uint32_t tr0, uint32_t tr1, uint32_t *table, td_launch_stats *stats, void *stream)
+{
+    g_err[0] = 0;
+    if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "td_collide_rows supports LTM and BB");
+    if (sched != TD_SCHED_GRID && sched != TD_SCHED_PERSISTENT)
+        return fail(TD_ERR_INVALID_ARG, "td_collide_rows takes the GRID or PERSISTENT schedule");
+    Plan p;
+    p.nb = static_cast<uint32_t>((uint64_t(n) + 31) / 32);
+    p.launches = 1;
+    td_status st = plan_rows(m, tr0, tr1, p);
+    if (st != TD_OK) return st;
+    if (!centers || !radii || !table) return fail(TD_ERR_INVALID_ARG, "centers, radii and table must be non-NULL");
+    if (!aligned16(table)) return fail(TD_ERR_INVALID_ARG, "table must be 16-byte aligned");
+    if ((reinterpret_cast<uintptr_t>(centers) | reinterpret_cast<uintptr_t>(radii)) & 3u)
+        return fail(TD_ERR_INVALID_ARG, "centers and radii must be 4-byte aligned");
+    if (sched == TD_SCHED_GRID && (p.blocks + 7) / 8 > kMaxGridX)
+        return fail(TD_ERR_UNSUPPORTED, "grid launch too large; use the persistent schedule");
+    uint64_t ctas = 0;
+    st = launch_collide(m, sched, centers, radii, n, slice_base(table, 32 * tri(tr0)), p,
+                        static_cast<cudaStream_t>(stream), &ctas);
+    fill_stats(stats, p, ctas);
+    return st;
 }
 
 td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_t *br0, uint32_t *br1, uint64_t *off0,

@@ -114,13 +114,13 @@ td_status launch(const Tiles &t, bool P, const int32_t *c, const int32_t *r, uin
 }  // namespace
 
 td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
-                         uint32_t *table, cudaStream_t st, uint64_t *ctas)
+                         uint32_t *table, const Plan &p, cudaStream_t st, uint64_t *ctas)
 {
     const bool P = s == TD_SCHED_PERSISTENT;
     const uint32_t nt = (n + 31) / 32;
-    if (m == TD_MAP_LTM) return launch(tiles::Ltm{tri(nt)}, P, c, r, n, table, st, ctas);
+    if (m == TD_MAP_LTM) return launch(tiles::ltm_source(p), P, c, r, n, table, st, ctas);
     if (m == TD_MAP_UTM_BLOCK) return launch(tiles::UtmBlk{tri(nt), nt}, P, c, r, n, table, st, ctas);
-    if (m == TD_MAP_BB) return launch(tiles::Bb{uint64_t(nt) * nt, nt}, P, c, r, n, table, st, ctas);
+    if (m == TD_MAP_BB) return launch(tiles::bb_source(p), P, c, r, n, table, st, ctas);
     return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM, BB and UTM-BLOCK");
 }
 

@@ -255,11 +255,11 @@ td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float
         return fail(TD_ERR_UNSUPPORTED, "the block-mapped strict distance map serves LTM and BB");
     }
     switch (m) {
-    case TD_MAP_LTM: return launch_tiles<tiles::Ltm, RHO, D>(tiles::Ltm{tri(p.nb)}, x, n, d, out, st, ctas);
+    case TD_MAP_LTM: return launch_tiles<tiles::Ltm, RHO, D>(tiles::ltm_source(p), x, n, d, out, st, ctas);
     case TD_MAP_UTM_BLOCK:
         return launch_tiles<tiles::UtmBlk, RHO, D>(tiles::UtmBlk{tri(p.nb), p.nb}, x, n, d, out, st, ctas);
     case TD_MAP_BB:
-        return launch_tiles<tiles::Bb, RHO, D>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, x, n, d, out, st, ctas);
+        return launch_tiles<tiles::Bb, RHO, D>(tiles::bb_source(p), x, n, d, out, st, ctas);
     case TD_MAP_REC: {
         for (uint32_t l = 1; l <= p.rec_k; ++l) {
             const uint32_t sb = (n >> l) / RHO, gx = n / (2 * RHO);

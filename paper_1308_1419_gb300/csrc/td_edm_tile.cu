@@ -46,11 +46,11 @@ td_status launch_rho(td_mapping m, bool P, const float *x, uint32_t n, uint32_t 
 {
     switch (m) {
     case TD_MAP_LTM:
-        return launch_tiles<tiles::Ltm, RHO, X2>(tiles::Ltm{tri(p.nb)}, P, x, n, d, out, st, ctas);
+        return launch_tiles<tiles::Ltm, RHO, X2>(tiles::ltm_source(p), P, x, n, d, out, st, ctas);
     case TD_MAP_UTM_BLOCK:
         return launch_tiles<tiles::UtmBlk, RHO, X2>(tiles::UtmBlk{tri(p.nb), p.nb}, P, x, n, d, out, st, ctas);
     case TD_MAP_BB:
-        return launch_tiles<tiles::Bb, RHO, X2>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, P, x, n, d, out, st, ctas);
+        return launch_tiles<tiles::Bb, RHO, X2>(tiles::bb_source(p), P, x, n, d, out, st, ctas);
     case TD_MAP_REC: {
         for (uint32_t l = 1; l <= p.rec_k; ++l) {
             const uint32_t sb = (n >> l) / RHO, gx = n / (2 * RHO);

@@ -30,8 +30,15 @@ struct Plan {
     uint32_t nb = 0;          // blocks per side, ceil(N / rho)
     uint32_t rec_k = 0;       // REC levels
     uint32_t rec_m = 0;       // REC diagonal triangle side
+    // a slice of the launch space (LTM and BB): units [slice_u0, slice_u0 + slice_units), the
+    // blocks of block rows [br0, br1) (plan_rows)
+    bool sliced = false;
+    uint64_t slice_u0 = 0, slice_units = 0;
 };
 td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, Plan &p);
+// Narrows a plan of LTM or BB to block rows [br0, br1), 0 <= br0 < br1 <= nb: LTM's units
+// [T(br0), T(br1)), BB's [br0 nb, br1 nb); blocks / useful / wasted become the slice's own.
+td_status plan_rows(td_mapping m, uint32_t br0, uint32_t br1, Plan &p);
 
 // Launchers (stream-ordered, no synchronisation).
 td_status launch_probe(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, uint32_t *out,
@@ -60,8 +67,9 @@ td_status launch_edm_pair(td_mapping m, td_schedule s, const float *x, uint32_t 
                           float *out, const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                            float *out, const Plan &p, bool x2, cudaStream_t st, uint64_t *ctas);
+// p: the tile plan (nb = ceil(n / 32) tiles per side, possibly sliced to tile rows).
 td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const int32_t *r, uint32_t n,
-                         uint32_t *table, cudaStream_t st, uint64_t *ctas);
+                         uint32_t *table, const Plan &p, cudaStream_t st, uint64_t *ctas);
 // Plan of the batched distance map, as td_edm_batched_run reads it from device memory: a
 // BatchHeader, the nprob + 1 exclusive prefix sums (uint64) of the problems' block counts
 // T(ceil(n/rho)) in launch-space order, then one BatchMeta per problem in that order.

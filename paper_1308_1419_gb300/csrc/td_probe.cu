@@ -166,11 +166,11 @@ template <int RHO, bool COVER>
 td_status launch_chunked_rho(td_mapping m, uint32_t N, uint32_t *out, const Plan &p, cudaStream_t st, uint64_t *ctas)
 {
     switch (m) {
-    case TD_MAP_LTM: return launch_chunked_tiles<tiles::Ltm, RHO, COVER>(tiles::Ltm{tri(p.nb)}, N, out, st, ctas);
+    case TD_MAP_LTM: return launch_chunked_tiles<tiles::Ltm, RHO, COVER>(tiles::ltm_source(p), N, out, st, ctas);
     case TD_MAP_UTM_BLOCK:
         return launch_chunked_tiles<tiles::UtmBlk, RHO, COVER>(tiles::UtmBlk{tri(p.nb), p.nb}, N, out, st, ctas);
     case TD_MAP_BB:
-        return launch_chunked_tiles<tiles::Bb, RHO, COVER>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, N, out, st, ctas);
+        return launch_chunked_tiles<tiles::Bb, RHO, COVER>(tiles::bb_source(p), N, out, st, ctas);
     case TD_MAP_REC: {
         for (uint32_t l = 1; l <= p.rec_k; ++l) {
             const uint32_t sb = (N >> l) / RHO, gx = N / (2 * RHO);

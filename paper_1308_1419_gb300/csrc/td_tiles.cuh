@@ -5,6 +5,7 @@
 #pragma once
 
 #include "td_device.cuh"
+#include "td_internal.h"
 
 namespace td {
 namespace tiles {
@@ -13,12 +14,17 @@ namespace tiles {
 // cap) continue the same block row -- (bi, bj), (bi, bj+1), ... when unit u is a block (ok) --
 // or are consecutive wasted units (when it is not).
 
-// g(lambda): unit = block index lambda < T(nb).
+// Sources with a unit offset u0 (LTM and BB) can walk a slice of their launch space: units
+// u0 .. u0 + units - 1.  A slice that starts and ends on block-row boundaries covers whole block
+// rows, which is how a triangle is split into the contiguous pieces of a partition.
+
+// g(lambda): unit = block index lambda = u0 + u < T(nb).
 struct Ltm {
     uint64_t units;
+    uint64_t u0 = 0;
     __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
     {
-        ltm_g(u, bi, bj);
+        ltm_g(u0 + u, bi, bj);
         return true;
     }
     __device__ __forceinline__ uint32_t run(uint64_t, bool, uint32_t bi, uint32_t bj, uint32_t cap) const
@@ -43,13 +49,16 @@ struct UtmBlk {
     }
 };
 
-// BB: unit = by * nb + bx over the n x n bounding box; blocks above the diagonal are skipped.
+// BB: unit = by * nb + bx = u0 + u over the n x n bounding box; blocks above the diagonal are
+// skipped.
 struct Bb {
     uint64_t units;
     uint32_t nb;
+    uint64_t u0 = 0;
     __device__ __forceinline__ bool operator()(uint64_t u, uint32_t &bi, uint32_t &bj) const
     {
-        const uint32_t by = static_cast<uint32_t>(u / nb), bx = static_cast<uint32_t>(u - uint64_t(by) * nb);
+        const uint64_t v = u0 + u;
+        const uint32_t by = static_cast<uint32_t>(v / nb), bx = static_cast<uint32_t>(v - uint64_t(by) * nb);
         bi = by;
         bj = bx;
         return bx <= by;
@@ -98,6 +107,14 @@ struct RecDiag {
         return ok ? min(cap, bi - bj + 1) : min(cap, mb - lb);  // to the diagonal / to the triangle's edge
     }
 };
+
+// The LTM and BB sources of a plan: its whole launch space, or the slice of block rows it was
+// planned for (td_internal.h, Plan::sliced).
+inline Ltm ltm_source(const Plan &p) { return p.sliced ? Ltm{p.slice_units, p.slice_u0} : Ltm{tri(p.nb), 0}; }
+inline Bb bb_source(const Plan &p)
+{
+    return p.sliced ? Bb{p.slice_units, p.nb, p.slice_u0} : Bb{uint64_t(p.nb) * p.nb, p.nb, 0};
+}
 
 }  // namespace tiles
 }  // namespace td

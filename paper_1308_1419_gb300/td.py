@@ -86,6 +86,9 @@ _c_collide_strict = _sig("td_collide_strict", _int, _vp, _vp, _u32, _vp, _vp)
 _c_edm_strict_blocks = _sig("td_edm_strict_blocks", _int, _int, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
 _c_collide_strict_blocks = _sig("td_collide_strict_blocks", _int, _int, _vp, _vp, _u32, _u32, _vp, _stats_p, _vp)
 _c_wait_selftest = _sig("td_wait_selftest", _int, _u32, _u64, _vp, C.POINTER(C.c_uint64), _vp)
+_c_map_probe_rows = _sig("td_map_probe_rows", _int, _int, _u32, _u32, _u32, _u32, _vp, _stats_p, _vp)
+_c_edm_rows = _sig("td_edm_rows", _int, _int, _int, _vp, _u32, _u32, _u32, _u32, _u32, _vp, _stats_p, _vp)
+_c_collide_rows = _sig("td_collide_rows", _int, _int, _int, _vp, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
 
 
 def _check(status):
@@ -171,6 +174,55 @@ def td_map_probe(mapping, schedule, N: int, rho: int, out: torch.Tensor = None, 
     st = td_launch_stats()
     _check(_c_map_probe(_mapping(mapping), _schedule(schedule), N, rho, ptr, C.byref(st), _stream(stream)))
     return out, st.as_dict()
+
+
+def _row_offset(b: int, rho: int, N: int) -> int:
+    r = min(b * rho, N)
+    return r * (r + 1) // 2
+
+
+def td_map_probe_rows(mapping, N: int, rho: int, br0: int, br1: int, out: torch.Tensor = None, stream=None):
+    """Probe of block rows [br0, br1) only (chunked schedule): the packed elements
+    [T(br0 rho), T(min(br1 rho, N))) of the whole output; returns (slice, stats)."""
+    size = _row_offset(br1, rho, N) - _row_offset(br0, rho, N)
+    if out is None:
+        out = torch.empty(max(size, 4), dtype=torch.int32, device="cuda")
+    op = _dev(out, torch.int32, size, "out")
+    st = td_launch_stats()
+    _check(_c_map_probe_rows(_mapping(mapping), N, rho, br0, br1, op, C.byref(st), _stream(stream)))
+    return out, st.as_dict()
+
+
+def td_edm_rows(mapping, schedule, x: torch.Tensor, rho: int, br0: int, br1: int, out: torch.Tensor = None,
+                stream=None):
+    """Distance map of block rows [br0, br1) of the points x (n x d); returns (slice, stats)."""
+    n, d = x.shape
+    xp = _dev(x, torch.float32, n * d, "x")
+    size = _row_offset(br1, rho, n) - _row_offset(br0, rho, n)
+    if out is None:
+        out = torch.empty(max(size, 4), dtype=torch.float32, device=x.device)
+    op = _dev(out, torch.float32, size, "out")
+    st = td_launch_stats()
+    _check(_c_edm_rows(_mapping(mapping), _schedule(schedule), xp, n, d, rho, br0, br1, op, C.byref(st),
+                       _stream(stream)))
+    return out, st.as_dict()
+
+
+def td_collide_rows(mapping, schedule, centers: torch.Tensor, radii: torch.Tensor, tr0: int, tr1: int,
+                    table: torch.Tensor = None, stream=None):
+    """Collision-table words of tile rows [tr0, tr1): words [32 T(tr0), 32 T(tr1)) of the whole
+    table; returns (slice, stats)."""
+    n = radii.numel()
+    cp = _dev(centers, torch.int32, 3 * n, "centers")
+    rp = _dev(radii, torch.int32, n, "radii")
+    words = 32 * (tr1 * (tr1 + 1) // 2 - tr0 * (tr0 + 1) // 2)
+    if table is None:
+        table = torch.empty(max(words, 4), dtype=torch.int32, device=radii.device)
+    tp = _dev(table, torch.int32, words, "table")
+    st = td_launch_stats()
+    _check(_c_collide_rows(_mapping(mapping), _schedule(schedule), cp, rp, n, tr0, tr1, tp, C.byref(st),
+                           _stream(stream)))
+    return table, st.as_dict()
 
 
 def td_map_dummy(mapping, schedule, N: int, rho: int, sink: torch.Tensor = None, stream=None):

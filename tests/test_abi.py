@@ -104,3 +104,29 @@ def test_oracle_not_imported_by_product():
         src = open(path, errors="ignore").read()
         assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
         assert "td_oracle" not in src and "liboracle" not in src, path
+
+
+def test_slice_arguments_rejected_before_launch():
+    """The block-row slice entry points validate on the host: empty or out-of-range row ranges,
+    strategies without contiguous block rows, wrong block sides and misaligned outputs return an
+    error before any launch (no GPU needed)."""
+    st = td.td_launch_stats()
+    probe = td._c_map_probe_rows
+    assert probe(4, 1024, 16, 3, 3, 256, C.byref(st), None) == 1          # empty range
+    assert probe(4, 1024, 16, 5, 2, 256, C.byref(st), None) == 1          # reversed
+    assert probe(4, 1024, 16, 0, 65, 256, C.byref(st), None) == 1         # past ceil(N / rho) = 64
+    assert probe(1, 1024, 16, 0, 1, 256, C.byref(st), None) == 2          # UTM: not a block strategy
+    assert probe(3, 1024, 16, 0, 1, 256, C.byref(st), None) == 2          # REC: block rows not contiguous
+    assert probe(4, 1024, 64, 0, 1, 256, C.byref(st), None) == 1          # the probe takes rho <= 32
+    assert probe(4, 1024, 16, 0, 1, 8, C.byref(st), None) == 1            # misaligned output
+    assert probe(4, 1024, 16, 0, 1, None, C.byref(st), None) == 1         # NULL output
+    edm = td._c_edm_rows
+    assert edm(4, 2, 256, 100, 4, 128, 0, 1, 256, C.byref(st), None) == 2  # chunked needs rho <= 32
+    assert edm(4, 1, 256, 100, 4, 16, 0, 1, 256, C.byref(st), None) == 2   # tiled needs rho 64 / 128
+    assert edm(4, 2, 256, 100, 0, 16, 0, 1, 256, C.byref(st), None) == 1   # d = 0
+    col = td._c_collide_rows
+    assert col(4, 1, 256, 256, 100, 2, 2, 256, C.byref(st), None) == 1    # empty tile-row range
+    assert col(4, 1, 256, 256, 100, 0, 5, 256, C.byref(st), None) == 1    # past ceil(100 / 32) = 4
+    assert col(8, 1, 256, 256, 100, 0, 1, 256, C.byref(st), None) == 2    # UTM-BLOCK not sliced
+    assert col(4, 2, 256, 256, 100, 0, 1, 256, C.byref(st), None) == 1    # CHUNKED not a collision schedule
+
