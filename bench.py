@@ -61,9 +61,19 @@ def probe_sources_digest():
     return h.hexdigest()
 
 
-def headline_config(sched):
+def sweep_slice(td, N, rho, ws, rank):
+    """This rank's block rows and packed slice of the triangle of side N: the td_partition share
+    (the whole triangle on one rank)."""
+    if ws == 1:
+        return 0, -(-N // rho), 0, tri(N)
+    return td.td_partition(N, rho, ws, rank)
+
+
+def headline_config(sched, ws=1):
     return {"workload": f"probe sweep: N in {{1024,4096,16384,65536}} x rho in {{8,16,32}}, g(lambda), {sched} schedule",
             "useful_pairs_per_step": sweep_pairs(),
+            "parallelism": "one GPU" if ws == 1 else
+            f"{ws} ranks, each the td_partition block-row slice of every triangle (no data-path collective)",
             "l2": "inputs none; each step's three N=65536 launches write 8.6 GB each (> 129 MB L2), "
                   "so L2 holds nothing of the previous step"}
 
@@ -218,7 +228,7 @@ def run_reference(args):
     v = pairs / dt
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic (no input; hash of (i, j))",
         "config": headline_config(args.sched),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -240,7 +250,19 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    out = torch.empty(tri(max(SIZES)), dtype=torch.int32, device=dev)
+    # Each rank's share of every triangle of the sweep: its block rows of the partition (contiguous
+    # lambda ranges, contiguous packed slices; no exchange between ranks).  One rank: the whole
+    # triangle through td_map_probe.
+    shard = {(N, rho): sweep_slice(td, N, rho, ws, rank) for N in SIZES for rho in RHOS}
+    out = torch.empty(max(4, max(o1 - o0 for _, _, o0, o1 in shard.values())), dtype=torch.int32, device=dev)
+
+    def probe_launch(strategy, sched, N, rho, buf):
+        if ws == 1:
+            return td.td_map_probe(strategy, sched, N, rho, buf)[1]
+        br0, br1, _, _ = shard[(N, rho)]
+        if br1 <= br0:
+            return {"launches": 0}
+        return td.td_map_probe_rows(strategy, N, rho, br0, br1, buf)[1]
 
     def barrier():
         if dist is not None:
@@ -253,7 +275,7 @@ def run_ours(args):
             for rho in RHOS:
                 if events is not None:
                     events[(N, rho)][0].record(stream)
-                _, st = td.td_map_probe(strategy, sched, N, rho, out)
+                st = probe_launch(strategy, sched, N, rho, out)
                 if events is not None:
                     events[(N, rho)][1].record(stream)
                 launches += st["launches"]
@@ -291,12 +313,12 @@ def run_ours(args):
     if dist is not None:
         dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
     ms = float(ms_t.item())
-    units = sweep_pairs() * args.steps * ws
+    units = sweep_pairs() * args.steps  # every rank has its share of the same sweep
     value = units / (ms / 1e3)
 
     # ---- compared strategies (same sweep), both schedules
     compare = {}
-    for strategy in ([] if args.no_compare else STRATS):
+    for strategy in ([] if args.no_compare or ws > 1 else STRATS):
         for sched in (("chunked", "persistent", "grid") if strategy in ("LTM", "BB", "REC", "UTM-BLOCK")
                       else ("persistent", "grid")):
             csteps = max(3, min(20, args.steps // 2))
@@ -315,7 +337,7 @@ def run_ours(args):
     # ---- write-only reference: cudaMemsetAsync of the same 8.6 GB (not a roofline denominator;
     # skipped with --no-compare so that a profiler's launch list holds only the timed step's kernels)
     memset_gbps = None
-    if not args.no_compare:
+    if not args.no_compare and ws == 1:
         for _ in range(3):
             out.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -332,7 +354,8 @@ def run_ours(args):
     per_rho = {}
     for r in RHOS:
         t = statistics.mean(per[(65536, r)])
-        per_rho[r] = {"ms": t, "GBps": 4 * tri(65536) / (t / 1e3) / 1e9}
+        _, _, o0, o1 = shard[(65536, r)]
+        per_rho[r] = {"ms": t, "GBps": 4 * (o1 - o0) / (t / 1e3) / 1e9}
     dom = max(RHOS, key=lambda r: per_rho[r]["ms"])
     achieved = per_rho[dom]["GBps"]
     traffic, traffic_note = None, "no ncu capture recorded for these kernel sources"
@@ -345,7 +368,7 @@ def run_ours(args):
                 "memset_write_GBps": memset_gbps,
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs, copy)" if peak_kind == "measured" else "fallback",
                 "per_rho": {str(r): v for r, v in per_rho.items()},
-                "algorithmic_bytes_per_launch": 4 * tri(65536)}
+                "algorithmic_bytes_per_launch": 4 * (shard[(65536, dom)][3] - shard[(65536, dom)][2])}
 
     # ---- end to end: the same sweep through the public API with the output in HOST memory.
     # Three ways: (copy) the kernel writes device memory and the result is copied to pinned host
@@ -354,20 +377,23 @@ def run_ours(args):
     # are kept in the line.
     e2e = None
     if not args.no_e2e:
-        host = torch.empty(tri(max(SIZES)), dtype=torch.int32, pin_memory=True)
-        d2h = sum(4 * tri(N) for N in SIZES for _ in RHOS)
+        host = torch.empty(out.numel(), dtype=torch.int32, pin_memory=True)
+        d2h = sum(4 * tri(N) for N in SIZES for _ in RHOS)  # all ranks' slices: the whole sweep
         e2e_steps = max(2, min(5, args.steps // 4))
+
+        def size(N, rho):
+            return shard[(N, rho)][3] - shard[(N, rho)][2]
 
         def e2e_copy():
             for N in SIZES:
                 for rho in RHOS:
-                    td.td_map_probe("LTM", args.sched, N, rho, out)
-                    host[: tri(N)].copy_(out[: tri(N)], non_blocking=True)
+                    probe_launch("LTM", args.sched, N, rho, out)
+                    host[: size(N, rho)].copy_(out[: size(N, rho)], non_blocking=True)
 
         def e2e_direct():
             for N in SIZES:
                 for rho in RHOS:
-                    td.td_map_probe("LTM", args.sched, N, rho, host)
+                    probe_launch("LTM", args.sched, N, rho, host)
 
         # (overlap) the kernel writes one of two device buffers while the previous result goes to
         # pinned host memory on a copy stream: the host link (~190 GB/s here) is the bound
@@ -381,10 +407,10 @@ def run_ours(args):
                 for rho in RHOS:
                     slot = slots[k % 2]
                     stream.wait_event(slot_free[k % 2])
-                    td.td_map_probe("LTM", args.sched, N, rho, slot)
+                    probe_launch("LTM", args.sched, N, rho, slot)
                     copy_stream.wait_stream(stream)
                     with torch.cuda.stream(copy_stream):
-                        host[: tri(N)].copy_(slot[: tri(N)], non_blocking=True)
+                        host[: size(N, rho)].copy_(slot[: size(N, rho)], non_blocking=True)
                         slot_free[k % 2].record(copy_stream)
                     k += 1
             stream.wait_stream(copy_stream)
@@ -397,7 +423,10 @@ def run_ours(args):
             for _ in range(e2e_steps):
                 fn()
             torch.cuda.synchronize()
-            modes[name] = sweep_pairs() * e2e_steps * ws / (time.perf_counter() - t0)
+            dt_t = torch.tensor([time.perf_counter() - t0], device=dev)
+            if dist is not None:
+                dist.all_reduce(dt_t, op=dist.ReduceOp.MAX)
+            modes[name] = sweep_pairs() * e2e_steps / float(dt_t.item())
         best = max(modes, key=modes.get)
         e2e = {"value": modes[best], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                "mode": best, "modes": modes}
@@ -407,15 +436,15 @@ def run_ours(args):
         cpu = cpu_oracle_sample()
 
     configs = None
-    if rank == 0 and not args.no_configs:
+    if rank == 0 and ws == 1 and not args.no_configs:
         configs = run_configs(args, td, stream)
 
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "u32", "data": "synthetic (no input array; each pair writes a hash of (i, j))",
-            "config": headline_config(args.sched),
+            "config": headline_config(args.sched, ws),
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "roofline": roofline,

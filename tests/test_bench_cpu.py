@@ -46,3 +46,18 @@ def test_cpu_rate_counts_every_item_it_ran():
     e = bench.cpu_baseline_entry(bench.probe_items(rows=64)[:4], 0.05, "pairs/s", "sample")
     assert e["cores"] == bench.host_cores() and e["all_cores"]["cores"] == e["cores"]
     assert e["one_core"]["cores"] == 1 and e["value"] == e["all_cores"]["value"] > 0
+
+
+def test_sweep_shards_cover_each_triangle_once():
+    """bench.py --gpus N: rank r computes its td_partition slice of every triangle of the sweep, so
+    the ranks' slices are disjoint, contiguous and add up to the whole sweep (strong scaling)."""
+    from paper_1308_1419_gb300.build import build_libtd
+    build_libtd()
+    from paper_1308_1419_gb300 import td
+    for ws in (1, 2, 3, 8):
+        for N in bench.SIZES:
+            for rho in bench.RHOS:
+                parts = [bench.sweep_slice(td, N, rho, ws, r) for r in range(ws)]
+                assert parts[0][2] == 0 and parts[-1][3] == bench.tri(N)
+                for a, b in zip(parts, parts[1:]):
+                    assert a[1] == b[0] and a[3] == b[2]
