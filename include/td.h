@@ -165,15 +165,17 @@ td_status td_partition(uint32_t N, uint32_t rho, uint32_t G, uint32_t r, uint32_
  * td_edm_rows: the distance map of td_edm (same summation order, bit-identical values) under
  *   TD_SCHED_CHUNKED with rho in {8, 16, 32} and d <= 8, or under TD_SCHED_GRID / PERSISTENT with
  *   rho in {64, 128} (the register-tiled body); x as in td_edm (all n points).
- * td_collide_rows: the collision table of td_collide over tile rows [tr0, tr1) of the tile
- *   triangle of side ceil(n / 32): the words [32 T(tr0), 32 T(tr1)) of the whole table, written
- *   to table[w - 32 T(tr0)]; sched GRID or PERSISTENT. */
+ * td_collide_rows: the collision table of td_collide over its block rows [br0, br1) (rho = 64: 64
+ *   spheres, two rows of 32 x 32 bit tiles, per block row): the tile rows [t0, t1),
+ *   t0 = min(2 br0, nt), t1 = min(2 br1, nt), nt = ceil(n / 32), i.e. the words [32 T(t0), 32 T(t1))
+ *   of the whole table, written to table[w - 32 T(t0)]; 0 <= br0 < br1 <= ceil(n / 64); sched GRID
+ *   or PERSISTENT. */
 td_status td_map_probe_rows(td_mapping m, uint32_t N, uint32_t rho, uint32_t br0, uint32_t br1, uint32_t *out,
                             td_launch_stats *stats, void *stream);
 td_status td_edm_rows(td_mapping m, td_schedule sched, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                       uint32_t br0, uint32_t br1, float *out, td_launch_stats *stats, void *stream);
 td_status td_collide_rows(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
-                          uint32_t tr0, uint32_t tr1, uint32_t *table, td_launch_stats *stats, void *stream);
+                          uint32_t br0, uint32_t br1, uint32_t *table, td_launch_stats *stats, void *stream);
 
 /* ------------------------------------------------------------------ mapping kernels */
 
@@ -244,15 +246,17 @@ td_status td_collide_strict_blocks(td_mapping m, const int32_t *centers, const i
 /* Collision table (collision detection is a td-problem named in the abstract and Sec. I):
  * spheres i > j collide iff |c_i - c_j|^2 <= (r_i + r_j)^2, decided exactly.  The table is
  * bit-packed in 32 x 32 bit-tiles over the tile triangle of side nt = ceil(n / 32): tile
- * (bi, bj), bj <= bi, is tile number T(bi) + bj and owns words [32 (T(bi)+bj), +32); word r of
- * it holds row i = 32 bi + r and its bit c (LSB first) holds column j = 32 bj + c.  Bits with
+ * (ti, tj), tj <= ti, is tile number T(ti) + tj and owns words [32 (T(ti)+tj), +32); word r of
+ * it holds row i = 32 ti + r and its bit c (LSB first) holds column j = 32 tj + c.  Bits with
  * i <= j, i >= n or j >= n are 0.  Every word of the table is written.
- * m: TD_MAP_LTM (tiles issued by g(lambda)) or TD_MAP_BB (bounding box of tiles); sched: GRID
- * or PERSISTENT.  One warp computes one tile.
- * centers: device, int32[n][3], each coordinate in [-2^30, 2^30); radii: device, int32[n], each
- * in [0, 16384] (inside these ranges the 32-bit evaluation equals the int64 definition;
- * outside them results are unspecified but every access stays in bounds).  Both 4-byte
- * aligned.  table: device, uint32[td_collide_words(n)], 16-byte aligned.  n = 0: no-op. */
+ * The launch space is the triangle of 64 x 64 blocks (four tiles each, three on the diagonal),
+ * m: TD_MAP_LTM (blocks issued by g(lambda)), TD_MAP_BB (their bounding box) or TD_MAP_UTM_BLOCK;
+ * sched: GRID or PERSISTENT.  One warp computes one block; stats count these blocks.
+ * centers: device, int32[n][3]; radii: device, int32[n]; any int32 values (the test is exact
+ * for all of them: 32-bit arithmetic for blocks whose coordinates lie in [-2^30, 2^30) and radii
+ * in [0, 2^14], 64/128-bit arithmetic otherwise; a negative radius enters only through
+ * (r_i + r_j)^2).  Both 4-byte aligned.  table: device, uint32[td_collide_words(n)], 16-byte
+ * aligned.  n = 0: no-op. */
 td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
                      uint32_t *table, td_launch_stats *stats, void *stream);
 

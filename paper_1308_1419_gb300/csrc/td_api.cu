@@ -362,11 +362,11 @@ td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, co
         return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM, BB and UTM-BLOCK");
     if (sched != TD_SCHED_GRID && sched != TD_SCHED_PERSISTENT)
         return fail(TD_ERR_INVALID_ARG, "td_collide takes the GRID or PERSISTENT schedule");
-    const uint64_t nt = (uint64_t(n) + 31) / 32;
+    const uint64_t nb = (uint64_t(n) + 63) / 64;  // the launch space: 64 x 64 blocks of four 32 x 32 bit tiles
     Plan p;
-    p.nb = static_cast<uint32_t>(nt);
-    p.blocks = m == TD_MAP_BB ? nt * nt : tri(nt);
-    p.useful = tri(nt);
+    p.nb = static_cast<uint32_t>(nb);
+    p.blocks = m == TD_MAP_BB ? nb * nb : tri(nb);
+    p.useful = tri(nb);
     p.launches = 1;
     if (n == 0) {
         fill_stats(stats, p, 0);
@@ -539,16 +539,16 @@ td_status td_edm_rows(td_mapping m, td_schedule sched, const float *x, uint32_t 
 }
 
 td_status td_collide_rows(td_mapping m, td_schedule sched, const int32_t *centers, const int32_t *radii, uint32_t n,
-                          uint32_t tr0, uint32_t tr1, uint32_t *table, td_launch_stats *stats, void *stream)
+                          uint32_t br0, uint32_t br1, uint32_t *table, td_launch_stats *stats, void *stream)
 {
     g_err[0] = 0;
     if (m != TD_MAP_LTM && m != TD_MAP_BB) return fail(TD_ERR_UNSUPPORTED, "td_collide_rows supports LTM and BB");
     if (sched != TD_SCHED_GRID && sched != TD_SCHED_PERSISTENT)
         return fail(TD_ERR_INVALID_ARG, "td_collide_rows takes the GRID or PERSISTENT schedule");
     Plan p;
-    p.nb = static_cast<uint32_t>((uint64_t(n) + 31) / 32);
+    p.nb = static_cast<uint32_t>((uint64_t(n) + 63) / 64);
     p.launches = 1;
-    td_status st = plan_rows(m, tr0, tr1, p);
+    td_status st = plan_rows(m, br0, br1, p);
     if (st != TD_OK) return st;
     if (!centers || !radii || !table) return fail(TD_ERR_INVALID_ARG, "centers, radii and table must be non-NULL");
     if (!aligned16(table)) return fail(TD_ERR_INVALID_ARG, "table must be 16-byte aligned");
@@ -557,7 +557,8 @@ td_status td_collide_rows(td_mapping m, td_schedule sched, const int32_t *center
     if (sched == TD_SCHED_GRID && (p.blocks + 7) / 8 > kMaxGridX)
         return fail(TD_ERR_UNSUPPORTED, "grid launch too large; use the persistent schedule");
     uint64_t ctas = 0;
-    st = launch_collide(m, sched, centers, radii, n, slice_base(table, 32 * tri(tr0)), p,
+    const uint64_t nt = (uint64_t(n) + 31) / 32, t0 = 2 * uint64_t(br0) < nt ? 2 * uint64_t(br0) : nt;
+    st = launch_collide(m, sched, centers, radii, n, slice_base(table, 32 * tri(t0)), p,
                         static_cast<cudaStream_t>(stream), &ctas);
     fill_stats(stats, p, ctas);
     return st;

@@ -18,8 +18,11 @@
 // exit (unused groups are computed and dropped) and written by lane 0.  The one word per row that
 // runs past the end of row i1 into the next row(s) is decided lane by lane from global memory.
 //
-// The predicate is collide_exact's.  When every coordinate of the run's spheres is below 2^23
-// in magnitude it is taken on the FP32 pipe (collide_f32_banded, one band for the run), and a row
+// The predicate is collide_exact's (exact for any int32 input).  When every coordinate and radius
+// of the run's spheres is below 2^23 in magnitude it is taken on the FP32 pipe
+// (collide_f32_banded, one band for the run; a radius that large or larger would not be exact
+// in FP32), after an exact pre-test that rules out a group of 32 pairs at once when each pair has
+// max(|dx|, |dy|) > |r_i + r_j|; a row
 // with a pair inside the band is decided again with the integer test (spheres reloaded, off the
 // fast path); otherwise the integer test decides every pair of the run (the staged values are
 // then the integers, bit for bit).
@@ -89,15 +92,20 @@ __device__ __forceinline__ void run_rows(const float4 *cols, const float4 *rows,
 #pragma unroll
         for (int g = 0; g < NW; ++g) {
             const float4 q4 = cols[q0 + 32 * g + lane];
-            bool hit;
             if (SMALL) {
-                bool near;
-                hit = collide_f32_banded(p, q4, band_c, near);
-                redo = redo || (near && uint32_t(g) < nfull);
+                // exact pre-test: max(|dx|, |dy|) > |r_i + r_j| rules the pair out; only a group
+                // with a pair passing it takes the banded test
+                const float e = fmaxf(fabsf(p.x - q4.x), fabsf(p.y - q4.y));
+                w[g] = 0;
+                if (__any_sync(0xffffffffu, e <= fabsf(p.w + q4.w))) {
+                    bool near;
+                    const bool hit = collide_f32_banded(p, q4, band_c, near);
+                    redo = redo || (near && uint32_t(g) < nfull);
+                    w[g] = __ballot_sync(0xffffffffu, hit);
+                }
             } else {
-                hit = collide_exact(bits_int4(p), bits_int4(q4));
+                w[g] = __ballot_sync(0xffffffffu, collide_exact(bits_int4(p), bits_int4(q4)));
             }
-            w[g] = __ballot_sync(0xffffffffu, hit);
         }
         if (SMALL && __any_sync(0xffffffffu, redo)) {  // a pair in the FP32 band: the row's words again, exactly
             const int4 pe = sphere(c, r, i1 + 1);
@@ -149,16 +157,16 @@ __global__ void __launch_bounds__(32 * kWarps) k_collide_chunked(Tiles tiles, ui
             for (uint32_t k = 0; k < kCols / 32; ++k) {
                 const uint32_t q = lane + 32 * k, j = jlo + q;
                 const int4 s4 = (q < span + 32 && j < n1) ? sphere(c, r, j) : make_int4(0, 0, 0, 0);
-                small = small && small_coords(s4);
-                rm = max(rm, uint32_t(s4.w));
+                small = small && small_sphere(s4);
+                rm = max(rm, uint32_t(abs(s4.w)));
                 cols[q] = as_float4(s4);
             }
             uint32_t rmr = 0;
             {
                 const uint32_t i1 = bi * RHO + lane;  // lane q < rho stages row sphere bi rho + q + 1
                 const int4 p4 = (lane < uint32_t(RHO) && i1 < n1) ? sphere(c, r, i1 + 1) : make_int4(0, 0, 0, 0);
-                small = small && small_coords(p4);
-                rmr = uint32_t(p4.w);
+                small = small && small_sphere(p4);
+                rmr = uint32_t(abs(p4.w));
                 rows[lane] = as_float4(p4);
             }
             const bool all_small = __all_sync(0xffffffffu, small);

@@ -208,19 +208,21 @@ def td_edm_rows(mapping, schedule, x: torch.Tensor, rho: int, br0: int, br1: int
     return out, st.as_dict()
 
 
-def td_collide_rows(mapping, schedule, centers: torch.Tensor, radii: torch.Tensor, tr0: int, tr1: int,
+def td_collide_rows(mapping, schedule, centers: torch.Tensor, radii: torch.Tensor, br0: int, br1: int,
                     table: torch.Tensor = None, stream=None):
-    """Collision-table words of tile rows [tr0, tr1): words [32 T(tr0), 32 T(tr1)) of the whole
-    table; returns (slice, stats)."""
+    """Collision-table words of block rows [br0, br1) (64 spheres each): tile rows
+    [t0, t1) = [min(2 br0, nt), min(2 br1, nt)), words [32 T(t0), 32 T(t1)); returns (slice, stats)."""
     n = radii.numel()
     cp = _dev(centers, torch.int32, 3 * n, "centers")
     rp = _dev(radii, torch.int32, n, "radii")
-    words = 32 * (tr1 * (tr1 + 1) // 2 - tr0 * (tr0 + 1) // 2)
+    nt = (n + 31) // 32
+    t0, t1 = min(2 * br0, nt), min(2 * br1, nt)
+    words = 32 * (t1 * (t1 + 1) // 2 - t0 * (t0 + 1) // 2)
     if table is None:
         table = torch.empty(max(words, 4), dtype=torch.int32, device=radii.device)
     tp = _dev(table, torch.int32, words, "table")
     st = td_launch_stats()
-    _check(_c_collide_rows(_mapping(mapping), _schedule(schedule), cp, rp, n, tr0, tr1, tp, C.byref(st),
+    _check(_c_collide_rows(_mapping(mapping), _schedule(schedule), cp, rp, n, br0, br1, tp, C.byref(st),
                            _stream(stream)))
     return table, st.as_dict()
 

@@ -34,7 +34,7 @@ def test_collide_benchmark_config_full_table(mapping, sched):
     got, st = _table(c, r, mapping, sched)
     want = oracle.collide(c, r)
     assert np.array_equal(got, want), int(np.count_nonzero(got != want))
-    assert st["useful_blocks"] == 1024 * 1025 // 2
+    assert st["useful_blocks"] == 512 * 513 // 2  # 64 x 64 blocks of four bit tiles
 
 
 @pytest.mark.parametrize("mapping,sched", VARIANTS)
@@ -93,3 +93,44 @@ def test_collide_many_exact_ties():
         for rho in (8, 32):
             bits, _ = td.td_collide_strict_blocks("LTM", ct, rt, rho)
             assert np.array_equal(bits[:words].cpu().numpy().view(np.uint32), oracle.collide_strict(c, r)), (n, rho)
+
+
+def _full_range_cases(seed):
+    """Coordinates and radii over the whole int32 range: squared distances and (r_i + r_j)^2 up to
+    about 2^64, exact ties and one-off misses at large magnitudes, negative radii (they enter only
+    through (r_i + r_j)^2), and the extreme corners where |r_i + r_j| = 2^32."""
+    rng = np.random.default_rng(seed)
+    lo, hi = -2**31, 2**31 - 1
+    c = [rng.integers(lo, hi, (160, 3), endpoint=True)]
+    r = [rng.integers(lo, hi, 160, endpoint=True)]
+    k = 2**28  # (3k, 4k, 0) at distance exactly 5k
+    c.append(np.array([[0, 0, 0], [3 * k, 4 * k, 0], [3 * k + 1, 4 * k, 0], [-3 * k, -4 * k, 7]]))
+    r.append(np.array([2 * k, 3 * k, 3 * k, -7 * k]))
+    c.append(np.array([[lo, lo, lo], [hi, hi, hi], [lo, hi, 0], [hi, lo, 0], [lo, lo, lo]]))
+    r.append(np.array([lo, lo, hi, hi, 0]))
+    base = rng.integers(-2**30, 2**30, 3)  # a cluster with radii of 2^29..2^30: many near-ties
+    c.append(base + rng.integers(-2**30, 2**30, (120, 3)))
+    r.append(rng.integers(2**29, 2**30, 120))
+    c = np.concatenate(c).clip(lo, hi).astype(np.int32)
+    r = np.concatenate(r).clip(lo, hi).astype(np.int32)
+    return c, r
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_collide_full_int32_range(seed):
+    """Every kernel form decides any int32 input exactly: the tiled table (both mappings, both
+    schedules), the element-level strict bits and the block-mapped strict bits."""
+    c, r = _full_range_cases(seed)
+    want = oracle.collide(c, r)
+    assert want.any()
+    for mapping, sched in VARIANTS:
+        got, _ = _table(c, r, mapping, sched)
+        assert np.array_equal(got, want), (mapping, sched, int(np.count_nonzero(got != want)))
+    ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+    words = td.td_collide_strict_words(r.size)
+    want_s = oracle.collide_strict(c, r)
+    got = td.td_collide_strict(ct, rt)[:words].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, want_s)
+    for rho in (8, 32):
+        bits, _ = td.td_collide_strict_blocks("LTM", ct, rt, rho)
+        assert np.array_equal(bits[:words].cpu().numpy().view(np.uint32), want_s), rho

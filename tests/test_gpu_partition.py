@@ -91,11 +91,12 @@ def test_collision_slices_rebuild_the_table(mapping):
     whole, _ = td.td_collide(mapping, "persistent", ct, rt)
     want = oracle.collide(c, r)
     assert np.array_equal(whole[:words].cpu().numpy().view(np.uint32), want)
+    nt = -(-n // 32)
     for G in (2, 3, 8):
         full = torch.full((words,), -1, dtype=torch.int32, device="cuda")
-        for tr0, tr1, _, _ in _slices(n, 32, G):
-            w0, w1 = 32 * _tri(tr0), 32 * _tri(tr1)
-            td.td_collide_rows(mapping, "persistent", ct, rt, tr0, tr1, full[w0:w1])
+        for br0, br1, _, _ in _slices(n, 64, G):   # block rows of 64 spheres: two tile rows each
+            w0, w1 = 32 * _tri(min(2 * br0, nt)), 32 * _tri(min(2 * br1, nt))
+            td.td_collide_rows(mapping, "persistent", ct, rt, br0, br1, full[w0:w1])
         assert torch.equal(full, whole[:words]), (mapping, G)
 
 
