@@ -110,7 +110,15 @@ typedef enum {
      * write longer contiguous runs; narrower ones balance better when there are few blocks);
      * otherwise a power of two in [128, 8192].  Output does not depend on it. */
     TD_OPT_PROBE_STRIP = 1,
-    TD_OPT_COUNT = 2
+    /* How the register-tiled distance map (td_edm, rho 64 / 128, and its slices) stages the
+     * block's points when d % 4 == 0 and x is 16-byte aligned: tensor-memory-accelerator box loads
+     * (cp.async.bulk.tensor, 16 features x rho points, issued by one thread into a two-stage
+     * mbarrier ring) or per-thread asynchronous 16-byte copies.  0 (default): TMA for d >= 64
+     * (measured a few per cent faster there; at d = 4 a box moves four times the bytes used and
+     * is slower); 1: TMA wherever possible; 2: per-thread copies only.  Same sums, bit-identical
+     * output. */
+    TD_OPT_EDM_TMA = 2,
+    TD_OPT_COUNT = 3
 } td_option;
 
 /* ------------------------------------------------------------------ host-only helpers */
@@ -282,6 +290,11 @@ td_status td_edm_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
  * TD_ERR_TIMEOUT if a pipeline wait ran out, else TD_OK; *fallback_pairs (host, may be NULL)
  * gets the number of pairs recomputed in the direct form. */
 td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *stream);
+
+/* Synchronises `stream` and reports whether a bounded wait of a kernel without a workspace (the
+ * TMA staging of td_edm, TD_OPT_EDM_TMA) ran out since the last call with clear = 1: TD_ERR_TIMEOUT
+ * if one did (that call's output is incomplete), else TD_OK.  clear: 1 resets the record. */
+td_status td_wait_status(int clear, void *stream);
 
 /* Self-test of the failure path of the bounded waits (the Gram pipeline's mbarrier waits): one
  * thread initialises an mbarrier expecting one arrival, arrives on it if `arrive` is 1, then

@@ -267,6 +267,10 @@ td_status td_set_option(td_option opt, int value)
     if (opt < 0 || opt >= TD_OPT_COUNT) return fail(TD_ERR_INVALID_ARG, "unknown option %d", int(opt));
     if (opt == TD_OPT_PROBE_STRIP && value != 0 && (value < 128 || value > 8192 || (value & (value - 1)) != 0))
         return fail(TD_ERR_INVALID_ARG, "probe strip width must be 0 or a power of two in [128, 8192] (got %d)", value);
+    if (opt == TD_OPT_EDM_F32X2 && value != 0 && value != 1)
+        return fail(TD_ERR_INVALID_ARG, "TD_OPT_EDM_F32X2 takes 0 or 1 (got %d)", value);
+    if (opt == TD_OPT_EDM_TMA && (value < 0 || value > 2))
+        return fail(TD_ERR_INVALID_ARG, "TD_OPT_EDM_TMA takes 0, 1 or 2 (got %d)", value);
     g_options[opt] = value;
     return TD_OK;
 }
@@ -477,6 +481,16 @@ td_status td_edm_gram_status(const void *ws, uint64_t *fallback_pairs, void *str
     if (s != TD_OK) return s;
     if (fallback_pairs) *fallback_pairs = fb;
     if (err != 0) return fail(TD_ERR_TIMEOUT, "td_edm_gram: a pipeline wait timed out (code %u)", err);
+    return TD_OK;
+}
+
+td_status td_wait_status(int clear, void *stream)
+{
+    g_err[0] = 0;
+    uint32_t code = 0;
+    const td_status s = read_wait_status(clear != 0, &code, static_cast<cudaStream_t>(stream));
+    if (s != TD_OK) return s;
+    if (code != 0) return fail(TD_ERR_TIMEOUT, "a bounded wait of the TMA-staged distance map ran out");
     return TD_OK;
 }
 

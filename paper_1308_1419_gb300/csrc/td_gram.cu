@@ -370,26 +370,6 @@ __global__ void __launch_bounds__(256, 4) k_gram_fix(const float *__restrict__ x
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn()
-{
-    static EncodeTiledFn fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
 struct GramLayout {
     size_t norms, xb, queue, counts, total;
     uint32_t gsize, seg;
@@ -427,8 +407,6 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     auto *xb = reinterpret_cast<__nv_bfloat16 *>(base + L.xb);
     auto *queue = reinterpret_cast<uint2 *>(base + L.queue);
     auto *seg_count = reinterpret_cast<uint32_t *>(base + L.counts);
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     td_status s = cuda_status(cudaMemsetAsync(status, 0, 16, st), "td_edm_gram status reset");
     if (s != TD_OK) return s;
     const uint32_t npad = (n + BM - 1) / BM * BM;
@@ -436,14 +414,9 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     s = launch_status("td_edm_gram prep kernel");
     if (s != TD_OK) return s;
     CUtensorMap tmap;
-    const cuuint64_t gdim[2] = {d, n};
-    const cuuint64_t gstride[1] = {cuuint64_t(d) * 2};
-    const cuuint32_t box[2] = {BK, BM};
-    const cuuint32_t estride[2] = {1, 1};
-    const CUresult r = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, xb, gdim, gstride, box, estride,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
+    s = encode_tiled_2d(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, xb, d, n, uint64_t(d) * 2, BK, BM,
+                        CU_TENSOR_MAP_SWIZZLE_128B);
+    if (s != TD_OK) return s;
     s = set_dynamic_smem_once(reinterpret_cast<const void *>(k_gram), SMEM_BYTES);
     if (s != TD_OK) return s;
     const uint32_t nt = (n + BM - 1) / BM;
@@ -463,6 +436,43 @@ td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cu
     if (s != TD_OK) return s;
     *err = h[0];
     *fallback = uint64_t(h[2]) | (uint64_t(h[3]) << 32);
+    return TD_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+td_status encode_tiled_2d(CUtensorMap *map, CUtensorMapDataType type, const void *base, uint64_t inner, uint64_t outer,
+                          uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swizzle)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t gdim[2] = {inner, outer};
+    const cuuint64_t gstride[1] = {row_bytes};
+    const cuuint32_t box[2] = {box_inner, box_outer};
+    const cuuint32_t estride[2] = {1, 1};
+    const CUresult r = enc(map, type, 2, const_cast<void *>(base), gdim, gstride, box, estride,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", int(r));
     return TD_OK;
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "td.h"
@@ -97,6 +98,13 @@ uint64_t batched_weight(uint32_t n, uint32_t d, uint32_t rho);
 uint64_t batched_fill_image(uint32_t nprob, const uint32_t *n, const uint32_t *d, uint32_t rho, const uint32_t *order,
                             uint64_t *x_off, uint64_t *out_off, unsigned char *img);
 size_t gram_workspace_bytes(uint32_t n, uint32_t d);
+// A 2-D tiled tensor map over a row-major array of `outer` rows of `inner` elements, rows
+// row_bytes apart (a multiple of 16), boxes of box_inner x box_outer elements, zero fill outside.
+td_status encode_tiled_2d(CUtensorMap *map, CUtensorMapDataType type, const void *base, uint64_t inner, uint64_t outer,
+                          uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swizzle);
+// Device word recording a bounded wait that ran out in a kernel without a workspace (the TMA
+// staging of the register-tiled distance map); read and cleared by td_wait_status.
+td_status read_wait_status(bool clear, uint32_t *code, cudaStream_t st);
 td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *ws, cudaStream_t st);
 td_status read_gram_status(const void *ws, uint32_t *err, uint64_t *fallback, cudaStream_t st);
 // One bounded mbarrier wait (arrive: whether its phase completes); copies {ran out, ns} to out

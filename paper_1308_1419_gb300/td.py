@@ -86,6 +86,7 @@ _c_collide_strict = _sig("td_collide_strict", _int, _vp, _vp, _u32, _vp, _vp)
 _c_edm_strict_blocks = _sig("td_edm_strict_blocks", _int, _int, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
 _c_collide_strict_blocks = _sig("td_collide_strict_blocks", _int, _int, _vp, _vp, _u32, _u32, _vp, _stats_p, _vp)
 _c_wait_selftest = _sig("td_wait_selftest", _int, _u32, _u64, _vp, C.POINTER(C.c_uint64), _vp)
+_c_wait_status = _sig("td_wait_status", _int, _int, _vp)
 _c_map_probe_rows = _sig("td_map_probe_rows", _int, _int, _u32, _u32, _u32, _u32, _vp, _stats_p, _vp)
 _c_edm_rows = _sig("td_edm_rows", _int, _int, _int, _vp, _u32, _u32, _u32, _u32, _u32, _vp, _stats_p, _vp)
 _c_collide_rows = _sig("td_collide_rows", _int, _int, _int, _vp, _vp, _u32, _u32, _u32, _vp, _stats_p, _vp)
@@ -130,7 +131,7 @@ def td_version() -> int:
     return int(_c_version())
 
 
-OPTIONS = {"edm_f32x2": 0, "probe_strip": 1}
+OPTIONS = {"edm_f32x2": 0, "probe_strip": 1, "edm_tma": 2}
 
 
 def td_set_option(opt, value: int):
@@ -442,6 +443,12 @@ def td_edm_gram_status(ws: torch.Tensor, stream=None) -> int:
     fb = C.c_uint64()
     _check(_c_gram_status(ws.data_ptr() + off, C.byref(fb), _stream(stream)))
     return int(fb.value)
+
+
+def td_wait_status(clear: bool = True, stream=None):
+    """Synchronises; raises TDError (TD_ERR_TIMEOUT) if a bounded wait of the TMA-staged distance
+    map ran out since the last clearing call."""
+    _check(_c_wait_status(1 if clear else 0, _stream(stream)))
 
 
 def td_wait_selftest(arrive: bool, limit_ns: int, ws: torch.Tensor = None, stream=None) -> int:

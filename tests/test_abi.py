@@ -94,6 +94,11 @@ def test_options_validated():
     assert td.td_get_option("probe_strip") == 1024
     td.td_set_option("probe_strip", 0)
     assert td._c_set_option(7, 0) == 1 and td.td_get_option(7) == 0          # unknown option
+    for bad in (-1, 3):
+        assert td._c_set_option(2, bad) == 1                                   # TMA staging: 0, 1 or 2
+    for v in (1, 2, 0):
+        td.td_set_option("edm_tma", v)
+        assert td.td_get_option("edm_tma") == v
 
 
 def test_oracle_not_imported_by_product():

@@ -205,3 +205,36 @@ def test_distance_sqrt_error_one_feature(sched, rho):
     ulp = np.abs(gi - ti)
     assert np.all(got[t == 0] == 0)
     assert int(ulp.max()) <= 2, (sched, int(ulp.max()), int((ulp > 0).sum()))
+
+
+@pytest.mark.parametrize("rho", [64, 128])
+def test_tma_staging_bit_identical(rho):
+    """TD_OPT_EDM_TMA = 1 (TMA box loads wherever possible) against 2 (per-thread asynchronous
+    copies only): the register-tiled body stages its points either way.  Same sums in the same order: the output must equal the
+    cp.async staging bit for bit (and the FP64 oracle within 2e-6), for ragged n, d not a
+    multiple of 16, every block strategy and both schedules, and for block-row slices."""
+    cases = [(1000, 64), (777, 128), (513, 256), (300, 260), (129, 4), (2000, 16), (4 * rho, 36)]
+    try:
+        for n, d in cases:
+            xh = synth.uniform_points(n, d, 9100 + n + d)
+            x = torch.from_numpy(xh).cuda()
+            want = oracle.edm(xh)
+            for mapping in ("LTM", "BB", "REC"):
+                if mapping == "REC" and n % rho:
+                    continue
+                for sched in ("grid", "persistent"):
+                    td.td_set_option("edm_tma", 2)
+                    ref, _ = td.td_edm(mapping, sched, x, rho)
+                    td.td_set_option("edm_tma", 1)
+                    got, _ = td.td_edm(mapping, sched, x, rho)
+                    assert torch.equal(got[: n * (n + 1) // 2], ref[: n * (n + 1) // 2]), (n, d, mapping, sched)
+            g = got[: n * (n + 1) // 2].cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(g - want) <= 2e-6 * want + 1e-30), (n, d)
+            nb = -(-n // rho)
+            if nb >= 3:
+                part, _ = td.td_edm_rows("LTM", "persistent", x, rho, 1, nb - 1)
+                lo, hi = (rho * (rho + 1)) // 2, min((nb - 1) * rho, n) * (min((nb - 1) * rho, n) + 1) // 2
+                assert torch.equal(part[: hi - lo], ref[lo:hi])
+        td.td_wait_status()  # no bounded wait ran out
+    finally:
+        td.td_set_option("edm_tma", 0)
