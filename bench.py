@@ -36,8 +36,8 @@ UNIT = "pairs/s"
 # they change the roofline line reports traffic as null until a new capture is taken.
 PROBE_SOURCES = ("td_probe.cu", "td_tiles.cuh", "td_device.cuh", "td_strategies.cuh")
 PROBE_TRAFFIC = {
-    "sources_sha256": "b9cad6f062d62191278d944d537a77f7ffb3017a3cc17a179be24ba328286d0f",
-    "bytes_per_launch": {8: 8540013824, 16: 8544059392, 32: 8547147776},
+    "sources_sha256": "7c71e11e0e12eaf89f6a291cf9cc1e6a6505ccc0d3d9521c76d727d4cbeefd9b",
+    "bytes_per_launch": {8: 8540655616, 16: 8545412352, 32: 8547297536},
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
                "-k regex:k_probe_chunked -s 3 -c 1 "
                "python bench.py --case probe:LTM:chunked:65536:<rho> --steps 1 --warmup 3",
