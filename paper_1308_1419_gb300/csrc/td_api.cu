@@ -174,6 +174,8 @@ td_status plan_rows(td_mapping m, uint32_t br0, uint32_t br1, Plan &p)
         return fail(TD_ERR_INVALID_ARG, "block rows [%u, %u) must satisfy br0 < br1 <= %u", br0, br1, p.nb);
     const uint64_t useful = tri(br1) - tri(br0);
     p.sliced = true;
+    p.slice_br0 = br0;
+    p.slice_br1 = br1;
     if (m == TD_MAP_LTM) {
         p.slice_u0 = tri(br0);
         p.slice_units = useful;

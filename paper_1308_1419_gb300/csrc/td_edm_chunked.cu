@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
             uint32_t bi, bj;
             const bool ok = tiles(u, bi, bj);
             const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(min(uend - u, uint64_t(rcap))));
-            u += run;
+            u += Tiles::kRuns ? 1u : run;
             if (!ok) continue;
             const uint32_t jlo = bj * RHO, ncol = run * RHO + 4;
             __syncwarp();  // the previous run's reads of the slice are done
@@ -223,11 +223,152 @@ __global__ void __launch_bounds__(32 * kWarps, 2) k_edm_chunked(Tiles tiles, uin
     }
 }
 
+// Column-aligned form for d <= 4.  Lane l of a warp computes the four columns b .. b + 3,
+// b = jlo + 124 m + 4 l (jlo a multiple of 4), for four element rows at a time: the columns' 4 d
+// coordinates are contiguous and 16-byte aligned in x (b d a multiple of 4), so they come as d
+// 16-byte loads (through L1, where every row of the run finds them) and serve 16 pairs.  The
+// packed offset T(i) + b is T(i) mod 4 past the 16-byte grid for every lane alike, so the run's
+// first aligned chunk of row i starts at column jlo + o_i, o_i = -T(i) mod 4, and the chunk of lane
+// l holds lane l's last 4 - o_i values and lane l + 1's first o_i values (o_i shuffles down);
+// lanes 0 .. 30 store, lane 31 only lends its values, so a step covers 124 columns.  Chunks that
+// run past the row end are left to the crossing pass, as in the staged form.
+template <int D>
+__device__ __forceinline__ void load_cols4(const float *__restrict__ x, uint32_t b, uint32_t np, float (&q)[4][D])
+{
+    if (b + 4 <= np) {
+        const float4 *p = reinterpret_cast<const float4 *>(x + uint64_t(b) * D);
+        float f[4 * D];
+#pragma unroll
+        for (int v = 0; v < D; ++v) {
+            const float4 t = __ldg(p + v);
+            f[4 * v] = t.x;
+            f[4 * v + 1] = t.y;
+            f[4 * v + 2] = t.z;
+            f[4 * v + 3] = t.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < D; ++k) q[c][k] = f[c * D + k];
+    } else {  // the last points of x: no read past its end
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < D; ++k) q[c][k] = b + c < np ? __ldg(x + uint64_t(b + c) * D + k) : 0.0f;
+    }
+}
+
+// The aligned chunk of one row from this lane's four values and the next lane's (o uniform).
+__device__ __forceinline__ float4 chunk_of(const float (&v)[4], uint32_t o)
+{
+    if (o == 0) return make_float4(v[0], v[1], v[2], v[3]);
+    if (o == 1) return make_float4(v[1], v[2], v[3], __shfl_down_sync(0xffffffffu, v[0], 1));
+    if (o == 2)
+        return make_float4(v[2], v[3], __shfl_down_sync(0xffffffffu, v[0], 1), __shfl_down_sync(0xffffffffu, v[1], 1));
+    return make_float4(v[3], __shfl_down_sync(0xffffffffu, v[0], 1), __shfl_down_sync(0xffffffffu, v[1], 1),
+                       __shfl_down_sync(0xffffffffu, v[2], 1));
+}
+
+constexpr int kRows = 4;  // element rows per step of the column-aligned form
+
+template <class Tiles, int RHO, int D, int SHIFT>
+__global__ void __launch_bounds__(32 * kWarps) k_edm_stream(Tiles tiles, uint32_t n, uint32_t S, uint32_t rcap,
+                                                            const float *__restrict__ x, float *__restrict__ out)
+{
+    static_assert(D >= 1 && D <= 4 && RHO % kRows == 0, "column-aligned form: 1 <= d <= 4");
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t np = n + SHIFT;  // points in x
+    const uint64_t warps = uint64_t(gridDim.x) * kWarps;
+    const uint64_t strips = (tiles.units + S - 1) / S;
+    for (uint64_t z = uint64_t(blockIdx.x) * kWarps + warp; z < strips; z += warps) {
+        const uint64_t uend = min(tiles.units, (z + 1) * S);
+        for (uint64_t u = z * S; u < uend;) {
+            uint32_t bi, bj;
+            const bool ok = tiles(u, bi, bj);
+            const uint32_t run = tiles.run(u, ok, bi, bj, static_cast<uint32_t>(min(uend - u, uint64_t(rcap))));
+            u += Tiles::kRuns ? 1u : run;
+            if (!ok) continue;
+            const uint32_t jlo = bj * RHO, jend = (bj + run) * RHO;
+            for (uint32_t r0 = 0; r0 < uint32_t(RHO); r0 += kRows) {
+                const uint32_t i0 = bi * RHO + r0;
+                if (i0 >= n) break;
+                float xi[kRows][D];
+                uint64_t ti[kRows];
+                uint32_t o[kRows], lim[kRows];  // lim: owned chunks start before column jlo + lim
+                uint32_t reach = 0;
+#pragma unroll
+                for (int a = 0; a < kRows; ++a) {
+                    const uint32_t i = i0 + a;
+                    ti[a] = tri(i);
+                    o[a] = (4u - (static_cast<uint32_t>(ti[a]) & 3u)) & 3u;
+                    lim[a] = i < n ? min(jend, i + 1) - jlo : 0u;
+                    reach = max(reach, lim[a] > o[a] ? lim[a] - o[a] : 0u);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) xi[a][k] = i < n ? __ldg(x + uint64_t(i + SHIFT) * D + k) : 0.0f;
+                }
+                for (uint32_t c0 = 0; c0 < reach; c0 += 124) {
+                    const uint32_t c = c0 + 4 * lane;  // local column of this lane's first value
+                    float q[4][D];
+                    load_cols4<D>(x, jlo + c, np, q);
+#pragma unroll
+                    for (int a = 0; a < kRows; ++a) {
+                        float v[4];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            float s = 0.0f;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) {
+                                const float t = xi[a][k] - q[m][k];
+                                s = fmaf(t, t, s);
+                            }
+                            v[m] = dist_sqrt(s);
+                        }
+                        const float4 w = chunk_of(v, o[a]);
+                        const uint32_t cs = c + o[a];  // local column of the chunk's first element
+                        if (lane < 31 && cs < lim[a] && jlo + cs + 3 <= i0 + a)
+                            __stcs(reinterpret_cast<float4 *>(out + ti[a] + jlo + cs), w);
+                    }
+                }
+            }
+            // crossing pass: lane r takes element row bi rho + r, whose last chunk runs past the row end
+            // unless the row ends on a 16-byte boundary; this run writes it if its first element lies
+            // in the run's columns of that row
+            if (lane < uint32_t(RHO)) {
+                const uint32_t i = bi * RHO + lane;
+                if (i < n) {
+                    const uint64_t t = tri(i), E = t + i + 1;
+                    const uint64_t Pc = (E - 1) & ~uint64_t(3);
+                    const uint32_t jc = static_cast<uint32_t>(Pc - t), jhi = min(jend, i + 1);
+                    if ((E & 3u) != 0 && Pc >= t && jc >= jlo && jc < jhi)
+                        crossing_chunk<D, SHIFT>(x, D, n, i, t, Pc, out);
+                }
+            }
+        }
+    }
+}
+
+template <class Tiles, int RHO, int D, int SHIFT = 0>
+td_status launch_stream(const Tiles &t, const float *x, uint32_t n, float *out, cudaStream_t st, uint64_t *ctas)
+{
+    if (t.units == 0) return TD_OK;
+    auto k = k_edm_stream<Tiles, RHO, D, SHIFT>;
+    const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, ~0ull) * kWarps;
+    const ChunkPlan cp = chunked_plan(t.units, RHO, resident, 2048, 8192);
+    const uint64_t strips = (t.units + cp.S - 1) / cp.S;
+    const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, (strips + kWarps - 1) / kWarps);
+    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, 0, st>>>(t, n, cp.S, cp.rcap, x, out);
+    *ctas += g;
+    return launch_status("td_edm chunked kernel (column-aligned)");
+}
+
 template <class Tiles, int RHO, int D, int SHIFT = 0>
 td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st,
                        uint64_t *ctas)
 {
     if (t.units == 0) return TD_OK;
+    // three and four features: the column-aligned form (measured faster there); one, two and more
+    // than four: the staged form
+    if (D == 3 || D == 4) return launch_stream<Tiles, RHO, (D == 4 ? 4 : 3), SHIFT>(t, x, n, out, st, ctas);
     auto k = k_edm_chunked<Tiles, RHO, D, SHIFT>;
     const uint32_t wmax = edm_chunk_wmax(d);
     const size_t smax = edm_chunk_smem(d, wmax);
@@ -244,18 +385,63 @@ td_status launch_tiles(const Tiles &t, const float *x, uint32_t n, uint32_t d, f
     return launch_status("td_edm chunked kernel");
 }
 
+// g(lambda) under the chunked schedule, by runs: the plan comes from the block count as for the
+// other sources, then the warps take runs of R = min(run cap, strip) blocks numbered by
+// tiles::LtmRuns, one run per strip, so that no run crosses the end of a block row (consecutive
+// lambda would cut a strip in two at every row end of the triangle).
+template <int RHO, int D, int SHIFT = 0>
+td_status launch_ltm_runs(const Plan &p, const float *x, uint32_t n, uint32_t d, float *out, cudaStream_t st,
+                          uint64_t *ctas)
+{
+    const uint64_t blocks = p.sliced ? p.slice_units : tri(p.nb);
+    if (blocks == 0) return TD_OK;
+    if (D == 3 || D == 4) {
+        auto k = k_edm_stream<tiles::LtmRuns, RHO, (D == 4 ? 4 : 3), SHIFT>;
+        const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, ~0ull) * kWarps;
+        const ChunkPlan cp = chunked_plan(blocks, RHO, resident, 2048, 8192);
+        uint32_t R = cp.S < cp.rcap ? cp.S : cp.rcap;
+        // a row's steps cover 124 columns each and its chunks reach 3 columns past the run: trim the
+        // run to the most blocks that still fit whole steps (16 -> 15 blocks at rho 16, 64 -> 61)
+        const uint32_t steps = (R * RHO + 3) / 124;
+        if (steps >= 1 && (steps * 124 - 3) / RHO >= 1) R = min(R, (steps * 124 - 3) / RHO);
+        if (R == 1)  // runs of one block: the blocks themselves, by g(lambda) alone
+            return launch_stream<tiles::Ltm, RHO, (D == 4 ? 4 : 3), SHIFT>(tiles::ltm_source(p), x, n, out, st, ctas);
+        const tiles::LtmRuns t = tiles::ltm_runs_source(p, R);
+        const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, (t.units + kWarps - 1) / kWarps);
+        k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, 0, st>>>(t, n, 1u, R, x, out);
+        *ctas += g;
+        return launch_status("td_edm chunked kernel (column-aligned, runs)");
+    }
+    auto k = k_edm_chunked<tiles::LtmRuns, RHO, D, SHIFT>;
+    const uint32_t wmax = edm_chunk_wmax(d);
+    const size_t smax = edm_chunk_smem(d, wmax);
+    td_status s = set_dynamic_smem_once(reinterpret_cast<const void *>(k), smax);
+    if (s != TD_OK) return s;
+    const uint64_t resident = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smax, ~0ull) * kWarps;
+    const ChunkPlan cp = chunked_plan(blocks, RHO, resident, wmax, wmax);
+    const uint32_t R = cp.S < cp.rcap ? cp.S : cp.rcap;
+    if (R == 1) return launch_tiles<tiles::Ltm, RHO, D, SHIFT>(tiles::ltm_source(p), x, n, d, out, st, ctas);
+    const tiles::LtmRuns t = tiles::ltm_runs_source(p, R);
+    const uint32_t sl = cp.W + kPad;
+    const size_t smem = edm_chunk_smem(d, cp.W);
+    const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, smem, (t.units + kWarps - 1) / kWarps);
+    k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, smem, st>>>(t, n, 1u, R, sl, x, d, out);
+    *ctas += g;
+    return launch_status("td_edm chunked kernel (runs)");
+}
+
 template <int RHO, int D>
 td_status launch_rho(td_mapping m, const float *x, uint32_t n, uint32_t d, float *out, const Plan &p, bool strict,
                      cudaStream_t st, uint64_t *ctas)
 {
     if (strict) {  // the strict triangle of n points = the packed triangle of side n - 1, rows shifted
-        if (m == TD_MAP_LTM) return launch_tiles<tiles::Ltm, RHO, D, 1>(tiles::Ltm{tri(p.nb)}, x, n - 1, d, out, st, ctas);
+        if (m == TD_MAP_LTM) return launch_ltm_runs<RHO, D, 1>(p, x, n - 1, d, out, st, ctas);
         if (m == TD_MAP_BB)
             return launch_tiles<tiles::Bb, RHO, D, 1>(tiles::Bb{uint64_t(p.nb) * p.nb, p.nb}, x, n - 1, d, out, st, ctas);
         return fail(TD_ERR_UNSUPPORTED, "the block-mapped strict distance map serves LTM and BB");
     }
     switch (m) {
-    case TD_MAP_LTM: return launch_tiles<tiles::Ltm, RHO, D>(tiles::ltm_source(p), x, n, d, out, st, ctas);
+    case TD_MAP_LTM: return launch_ltm_runs<RHO, D>(p, x, n, d, out, st, ctas);
     case TD_MAP_UTM_BLOCK:
         return launch_tiles<tiles::UtmBlk, RHO, D>(tiles::UtmBlk{tri(p.nb), p.nb}, x, n, d, out, st, ctas);
     case TD_MAP_BB:

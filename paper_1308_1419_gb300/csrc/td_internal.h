@@ -35,6 +35,7 @@ struct Plan {
     // blocks of block rows [br0, br1) (plan_rows)
     bool sliced = false;
     uint64_t slice_u0 = 0, slice_units = 0;
+    uint32_t slice_br0 = 0, slice_br1 = 0;
 };
 td_status plan_strategy(td_mapping m, td_schedule s, uint32_t N, uint32_t rho, Plan &p);
 // Narrows a plan of LTM or BB to block rows [br0, br1), 0 <= br0 < br1 <= nb: LTM's units
