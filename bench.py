@@ -36,8 +36,8 @@ UNIT = "pairs/s"
 # they change the roofline line reports traffic as null until a new capture is taken.
 PROBE_SOURCES = ("td_probe.cu", "td_tiles.cuh", "td_device.cuh", "td_strategies.cuh")
 PROBE_TRAFFIC = {
-    "sources_sha256": "7c71e11e0e12eaf89f6a291cf9cc1e6a6505ccc0d3d9521c76d727d4cbeefd9b",
-    "bytes_per_launch": {8: 8540655616, 16: 8545412352, 32: 8547297536},
+    "sources_sha256": "99d0ef2a15609836a27a658e98bce57d1eadbbb81a39851515023b1a8bd82f2a",
+    "bytes_per_launch": {8: 8540654080, 16: 8545221120, 32: 8546967552},
     "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none "
                "-k regex:k_probe_chunked -s 3 -c 1 "
                "python bench.py --case probe:LTM:chunked:65536:<rho> --steps 1 --warmup 3",
