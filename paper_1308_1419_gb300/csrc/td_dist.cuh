@@ -1,4 +1,6 @@
-// td_dist.cuh -- the square root shared by every FP32 direct distance kernel.
+// td_dist.cuh -- the square root shared by every FP32 direct distance kernel, and the packed
+// two-lane FP32 operations (sub.rn.f32x2 / fma.rn.f32x2, sm_100+) some of them use: each lane
+// of a packed operation is rounded exactly as the scalar operation would be.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,6 +18,32 @@ __device__ __forceinline__ float dist_sqrt(float s)
 {
     float r;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ void unpack2(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+__device__ __forceinline__ unsigned long long sub_f32x2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long fma_f32x2(unsigned long long a, unsigned long long b, unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
 
