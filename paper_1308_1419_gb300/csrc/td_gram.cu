@@ -85,13 +85,15 @@ __device__ __forceinline__ float sqrt_approx(float v)
 
 // BF16 copy of the points and FP32 squared norms; one warp per point.  The norms are padded
 // with zeros up to npad (a whole number of blocks), so the epilogue reads them unchecked.  Also
-// clears the counters of the recompute queue's regions.
+// clears the counters of the recompute queue's regions and the status block (the first kernel of
+// the call, so no separate memset is needed).
 __global__ void __launch_bounds__(256) k_gram_prep(const float *__restrict__ x, uint32_t n, uint32_t npad,
                                                    uint32_t d, __nv_bfloat16 *__restrict__ xb,
                                                    float *__restrict__ norms, uint32_t *__restrict__ qcount,
-                                                   uint64_t regions)
+                                                   uint64_t regions, uint32_t *__restrict__ status)
 {
     const uint32_t gid = blockIdx.x * blockDim.x + threadIdx.x, warp = gid >> 5, lane = threadIdx.x & 31;
+    if (gid < 4) status[gid] = 0;  // error word, reserved word, recomputed pairs
     for (uint64_t k = gid; k < regions; k += uint64_t(gridDim.x) * blockDim.x) qcount[k] = 0;
     if (warp >= n) {
         if (warp < npad && lane == 0) norms[warp] = 0.0f;
@@ -554,11 +556,9 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     auto *xb = reinterpret_cast<__nv_bfloat16 *>(base + L.xb);
     auto *queue = reinterpret_cast<uint2 *>(base + L.queue);
     auto *qcount = reinterpret_cast<uint32_t *>(base + L.counts);
-    td_status s = cuda_status(cudaMemsetAsync(status, 0, 16, st), "td_edm_gram status reset");
-    if (s != TD_OK) return s;
     const uint32_t npad = (n + BM - 1) / BM * BM;
-    k_gram_prep<<<(npad + 7) / 8, 256, 0, st>>>(x, n, npad, d, xb, norms, qcount, L.regions);
-    s = launch_status("td_edm_gram prep kernel");
+    k_gram_prep<<<(npad + 7) / 8, 256, 0, st>>>(x, n, npad, d, xb, norms, qcount, L.regions, status);
+    td_status s = launch_status("td_edm_gram prep kernel");
     if (s != TD_OK) return s;
     CUtensorMap tmap;
     s = encode_tiled_2d(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, xb, d, n, uint64_t(d) * 2, BK, BM,
