@@ -66,7 +66,7 @@ constexpr uint32_t QQ = 32 * BM / 32;
 // The recompute takes the blocks of block row b (lambda = T(b) .. T(b) + b) in runs of FIX_R, so
 // the row has b / FIX_R + 1 parts (its work grows with b); fix_units(b) = the parts of block rows
 // 0 .. b - 1 = b + FIX_R q (q - 1) / 2 + r q, b = q FIX_R + r.
-constexpr uint32_t FIX_R = 8;
+constexpr uint32_t FIX_R = 16;
 __host__ __device__ __forceinline__ uint64_t fix_units(uint32_t b)
 {
     const uint64_t q = b / FIX_R, r = b % FIX_R;
@@ -123,6 +123,10 @@ __device__ float direct_distance(const float *__restrict__ x, uint32_t d, uint32
     return dist_sqrt(s);
 }
 
+// kNormAhead (d <= 64, one k-step per block): the block's MMA is short, and the epilogue would wait
+// on its norm loads; the next block's norm lines are prefetched into L1 one block ahead.  (With more
+// k-steps the MMA covers those loads, and the instantiation without the prefetch is faster.)
+template <bool kNormAhead>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gram(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ x, const float *__restrict__ norms,
            uint32_t n, uint32_t d, uint32_t nt, float *__restrict__ out, uint2 *__restrict__ queue,
@@ -264,6 +268,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             // norms do not depend on the accumulator: their loads go out before the wait for it (the
             // norms are zero-padded to whole blocks, so the 16-byte loads need no bounds)
             const uint32_t jb = bj * BM + 32 * q, j = jb + lane, ib = bi * BM + c0;
+            if (kNormAhead && lam + gridDim.x < tiles && lane < 2) {  // the next block's norm lines
+                uint32_t bi2, bj2;
+                ltm_g(lam + gridDim.x, bi2, bj2);
+                const float *nl = norms + (lane ? bi2 * BM + c0 : bj2 * BM + 32 * q);
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(nl));
+            }
             const float nj = __ldg(norms + j);
             float4 nq[8];
             const float4 *ni4 = reinterpret_cast<const float4 *>(norms + ib);
@@ -564,10 +574,16 @@ td_status launch_gram(const float *x, uint32_t n, uint32_t d, float *out, void *
     s = encode_tiled_2d(&tmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, xb, d, n, uint64_t(d) * 2, BK, BM,
                         CU_TENSOR_MAP_SWIZZLE_128B);
     if (s != TD_OK) return s;
-    s = set_dynamic_smem_once(reinterpret_cast<const void *>(k_gram), SMEM_BYTES);
+    const bool ahead = d <= BK;
+    s = set_dynamic_smem_once(ahead ? reinterpret_cast<const void *>(k_gram<true>)
+                                    : reinterpret_cast<const void *>(k_gram<false>),
+                              SMEM_BYTES);
     if (s != TD_OK) return s;
     const uint32_t nt = (n + BM - 1) / BM;
-    k_gram<<<dim3(L.gsize), THREADS, SMEM_BYTES, st>>>(tmap, x, norms, n, d, nt, out, queue, qcount, status);
+    if (ahead)
+        k_gram<true><<<dim3(L.gsize), THREADS, SMEM_BYTES, st>>>(tmap, x, norms, n, d, nt, out, queue, qcount, status);
+    else
+        k_gram<false><<<dim3(L.gsize), THREADS, SMEM_BYTES, st>>>(tmap, x, norms, n, d, nt, out, queue, qcount, status);
     s = launch_status("td_edm_gram kernel");
     if (s != TD_OK) return s;
     auto *fallback = reinterpret_cast<unsigned long long *>(status + 2);
