@@ -123,10 +123,12 @@ __device__ float direct_distance(const float *__restrict__ x, uint32_t d, uint32
     return dist_sqrt(s);
 }
 
-// kNormAhead (d <= 64, one k-step per block): the block's MMA is short, and the epilogue would wait
-// on its norm loads; the next block's norm lines are prefetched into L1 one block ahead.  (With more
-// k-steps the MMA covers those loads, and the instantiation without the prefetch is faster.)
-template <bool kNormAhead>
+// kOneStep (d <= 64, one k-step per block): the block's MMA is short, and the epilogue would wait
+// on its norm loads, so the next block's norm lines are prefetched into L1 one block ahead, and an
+// interior block's rows are stored after all 32 distances are formed.  With more k-steps the MMA
+// covers the norm loads, and the rows are stored as they are formed, interleaved with the square
+// roots.  (Each choice measured faster in its own range: n = 16384, d = 64 and d = 256.)
+template <bool kOneStep>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gram(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ x, const float *__restrict__ norms,
            uint32_t n, uint32_t d, uint32_t nt, float *__restrict__ out, uint2 *__restrict__ queue,
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             // norms do not depend on the accumulator: their loads go out before the wait for it (the
             // norms are zero-padded to whole blocks, so the 16-byte loads need no bounds)
             const uint32_t jb = bj * BM + 32 * q, j = jb + lane, ib = bi * BM + c0;
-            if (kNormAhead && lam + gridDim.x < tiles && lane < 2) {  // the next block's norm lines
+            if (kOneStep && lam + gridDim.x < tiles && lane < 2) {  // the next block's norm lines
                 uint32_t bi2, bj2;
                 ltm_g(lam + gridDim.x, bi2, bj2);
                 const float *nl = norms + (lane ? bi2 * BM + c0 : bj2 * BM + 32 * q);
@@ -297,15 +299,36 @@ __global__ void __launch_bounds__(THREADS, 1)
             // d2 - kCancel s2 is shifted into `neg` (row c at bit 31 - c).  A pair with d2 < 0 always
             // cancels, so the NaN its square root gives is rewritten later.
             uint32_t neg = 0;
+            if constexpr (!kOneStep) {
+                // each interior row's 128 bytes leave as soon as they are formed
+                float *p = out + tri(ib) + j;  // row ib + c at p, then p += ib + c + 1
+                uint32_t step = ib + 1;
 #pragma unroll
-            for (uint32_t c4 = 0; c4 < 8; ++c4) {
-                const float ni[4] = {nq[c4].x, nq[c4].y, nq[c4].z, nq[c4].w};
+                for (uint32_t c4 = 0; c4 < 8; ++c4) {
+                    const float ni[4] = {nq[c4].x, nq[c4].y, nq[c4].z, nq[c4].w};
 #pragma unroll
-                for (uint32_t k = 0; k < 4; ++k) {
-                    const float s2 = ni[k] + nj;
-                    const float d2 = fmaf(-2.0f, v[4 * c4 + k], s2);
-                    neg = __funnelshift_l(__float_as_uint(fmaf(-kCancel, s2, d2)), neg, 1);
-                    v[4 * c4 + k] = sqrt_approx(d2);
+                    for (uint32_t k = 0; k < 4; ++k) {
+                        const float s2 = ni[k] + nj;
+                        const float d2 = fmaf(-2.0f, v[4 * c4 + k], s2);
+                        neg = __funnelshift_l(__float_as_uint(fmaf(-kCancel, s2, d2)), neg, 1);
+                        v[4 * c4 + k] = sqrt_approx(d2);
+                        if (interior) {
+                            *p = v[4 * c4 + k];
+                            p += step++;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (uint32_t c4 = 0; c4 < 8; ++c4) {
+                    const float ni[4] = {nq[c4].x, nq[c4].y, nq[c4].z, nq[c4].w};
+#pragma unroll
+                    for (uint32_t k = 0; k < 4; ++k) {
+                        const float s2 = ni[k] + nj;
+                        const float d2 = fmaf(-2.0f, v[4 * c4 + k], s2);
+                        neg = __funnelshift_l(__float_as_uint(fmaf(-kCancel, s2, d2)), neg, 1);
+                        v[4 * c4 + k] = sqrt_approx(d2);
+                    }
                 }
             }
             uint32_t mask = __brev(neg);  // bit c: pair (ib + c, j) cancels
@@ -314,8 +337,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t below = hi >= 32u ? 0xffffffffu : ((1u << hi) - 1u);
                 mask &= lo >= 32u ? 0u : (below & (0xffffffffu << lo));
             }
-            // write-out: row ib + c, lane = column, 128 contiguous bytes per row and store instruction
-            if (interior) {
+            // write-out (the rest): row ib + c, lane = column, 128 contiguous bytes per row and store instruction
+            if (kOneStep && interior) {
                 float *p = out + tri(ib) + j;
                 uint32_t step = ib + 1;  // T(r + 1) - T(r) = r + 1
 #pragma unroll
@@ -323,7 +346,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     *p = v[c];
                     p += step;
                 }
-            } else {
+            } else if (!interior) {
 #pragma unroll
                 for (uint32_t c = 0; c < 32; ++c) {
                     const uint32_t i2 = ib + c;
