@@ -270,8 +270,9 @@ td_status td_collide(td_mapping m, td_schedule sched, const int32_t *centers, co
 
 /* ------------------------------------------------------------------ Gram-form distance map */
 
-/* Bytes of device workspace td_edm_gram needs: a status block, n FP32 squared norms and a BF16
- * copy of the n x d points. */
+/* Bytes of device workspace td_edm_gram needs: a status block, n FP32 squared norms, a BF16
+ * copy of the n x d points, and the recompute queue (room for 1/32 of the pairs of every
+ * 128 x 128 block, 8 bytes a pair, with a counter per 32-row quarter of a block). */
 size_t td_edm_gram_workspace(uint32_t n, uint32_t d);
 
 /* Euclidean distance map in Gram form on the tensor cores: D(i,j)^2 = |x_i|^2 + |x_j|^2 -
