@@ -7,7 +7,8 @@
 // direct FP32 form sum_k (x_i[k] - x_j[k])^2 from the FP32 points.
 //
 // Three kernels, stream-ordered:
-//   k_gram_prep  BF16 copy of the points and FP32 squared norms.
+//   k_gram_prep  BF16 copy of the points and FP32 squared norms; clears the queue counters and the
+//                status block.
 //   k_gram       persistent, warp-specialised, one CTA per SM; 128 x 128 blocks of the packed lower
 //                triangle issued by g(lambda) over the block triangle of side ceil(n / 128)
 //                (Sec. II-A), every role walking the same block sequence:
