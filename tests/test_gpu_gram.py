@@ -78,6 +78,29 @@ def test_gram_precision_workload():
     assert torch.allclose(out[close], ref[close], rtol=4e-6, atol=0)
 
 
+@pytest.mark.parametrize("n,d", [(4096, 64), (2048, 256)])
+def test_gram_queue_regions_half_full(n, d):
+    """16 clusters: 1/16 of the pairs cancel, twice what a queue region holds (1/32 of its block
+    quarter's pairs).  In the same warp some cancelling pairs then land in the queue and the rest
+    are recomputed by the epilogue itself; both must meet the FP32 tolerance.  d = 64 and d = 256
+    run the two forms of the main pass."""
+    xh = synth.clustered_points(n, d, clusters=16, sigma=0.05, seed=9100 + d)
+    x = torch.from_numpy(xh).cuda()
+    out, ws = td.td_edm_gram(x)
+    fb = td.td_edm_gram_status(ws)
+    total = n * (n + 1) // 2
+    assert 0.5 / 16 * total < fb < 2.0 / 16 * total, fb
+    rng = np.random.default_rng(d)
+    ii = rng.integers(0, n, 200000).astype(np.uint32)
+    jj = (rng.random(200000) * (ii + 1)).astype(np.uint32)
+    _check_pairs(xh, out, ii, jj)
+    # every pair that cancels takes the direct form, queued or not: against the FP32 direct kernel
+    ref, _ = td.td_edm("LTM", "persistent", x, 128)
+    close = ref < 0.1 * torch.sqrt(torch.tensor(2.0 * d))
+    assert int(close.sum()) > 0.5 / 16 * total
+    assert torch.allclose(out[: total][close[: total]], ref[: total][close[: total]], rtol=4e-6, atol=0)
+
+
 def test_gram_rejects():
     x = torch.zeros(10, 12, device="cuda")
     with pytest.raises(td.TDError):
