@@ -135,3 +135,34 @@ def test_slice_arguments_rejected_before_launch():
     assert col(8, 1, 256, 256, 100, 0, 1, 256, C.byref(st), None) == 2    # UTM-BLOCK not sliced
     assert col(4, 2, 256, 256, 100, 0, 1, 256, C.byref(st), None) == 1    # CHUNKED not a collision schedule
 
+
+
+def test_empty_inputs_are_noops():
+    """Every entry point documents an empty input (N = 0, n = 0, n < 2 for the strict forms,
+    nprob = 0) as a no-op: it returns TD_OK before any check of the (here NULL) buffers and before
+    any launch, so it needs no GPU, and its stats report no launched CTA."""
+    st = td.td_launch_stats()
+    for m in ("LTM", "BB", "UTM", "RB"):
+        for sched in (0, 1):
+            st.ctas = 7
+            assert td._c_map_probe(td.MAPPINGS[m], sched, 0, 16, None, C.byref(st), None) == 0, (m, sched)
+            assert st.ctas == 0 and st.useful_blocks == 0
+            st.ctas = 7
+            assert td._c_edm(td.MAPPINGS[m], sched, None, 0, 3, 16, None, C.byref(st), None) == 0, (m, sched)
+            assert st.ctas == 0
+    assert td._c_map_probe(td.MAPPINGS["LTM"], 2, 0, 16, None, C.byref(st), None) == 0        # chunked
+    assert td._c_edm(td.MAPPINGS["LTM"], 1, None, 0, 64, 128, None, C.byref(st), None) == 0   # tiled
+    for m in ("LTM", "BB"):
+        st.ctas = 7
+        assert td._c_collide(td.MAPPINGS[m], 0, None, None, 0, None, C.byref(st), None) == 0
+        assert st.ctas == 0
+    for n in (0, 1):
+        assert td._c_edm_strict(None, n, 3, None, None) == 0
+        assert td._c_collide_strict(None, None, n, None, None) == 0
+        assert td._c_edm_strict_blocks(td.MAPPINGS["LTM"], None, n, 3, 16, None, C.byref(st), None) == 0
+        assert td._c_collide_strict_blocks(td.MAPPINGS["LTM"], None, None, n, 32, None, C.byref(st), None) == 0
+    assert td._c_gram(None, 0, 256, None, None, 0, None) == 0
+    cfg = td.td_batched_config(128, 0)
+    assert td._c_batched(0, None, None, None, None, None, 0, C.byref(cfg), C.byref(st), None) == 0
+    assert td._c_batched_noalloc(0, None, None, None, None, C.byref(cfg), C.byref(st), None) == 0
+    assert st.ctas == 0
