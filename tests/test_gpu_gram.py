@@ -41,7 +41,8 @@ def _check_pairs(xh, out, ii, jj):
     return float(rel.max()), float(np.sqrt((rel ** 2).mean()))
 
 
-@pytest.mark.parametrize("n,d", [(1, 8), (37, 8), (128, 64), (300, 64), (257, 200), (640, 256), (300, 520), (200, 1024)])
+@pytest.mark.parametrize("n,d", [(1, 8), (37, 8), (128, 64), (300, 64), (257, 200), (640, 256), (300, 520), (200, 1024),
+                                 (130, 8192)])
 def test_gram_small_all_pairs(n, d):
     xh = synth.uniform_points(n, d, 7000 + n + d)
     xh[n // 3] = xh[n // 5]  # a duplicated point: distance exactly 0 through the recompute
