@@ -77,6 +77,30 @@ def test_edm_ragged_all_kernels(d):
                     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (n, d, rho, mapping, sched)
 
 
+@pytest.mark.parametrize("d", [4096, 4097])
+def test_edm_many_features(d):
+    """d has no upper limit: at d = 4096 the tiled kernels stage the points as TMA boxes, at d = 4097
+    (not a multiple of 4) feature by feature; the one-element-per-thread kernel loops over all d.
+    n = 300 leaves ragged block rows at every rho.  Bit-identical across kernels; against the oracle
+    within the bound of the documented FP32 order rather than 2e-6: d sequential FMAs of rounded
+    differences put at most (d + 2) u on D^2 (u = 2^-24), half that on D, plus 2 ulp of the square
+    root."""
+    n = 300
+    xh = synth.uniform_points(n, d, 4000 + d)
+    want = oracle.edm(xh)
+    rtol = ((d + 2) / 2 + 3) * 2.0 ** -24
+    x = torch.from_numpy(xh).cuda()
+    ref = None
+    for mapping, sched, rho in [("LTM", "persistent", 128), ("LTM", "grid", 64), ("BB", "persistent", 128),
+                                ("LTM", "persistent", 16), ("UTM", "grid", 16)]:
+        got, _ = _edm(mapping, sched, x, rho)
+        err = np.abs(np.asarray(got, dtype=np.float64) - want)
+        assert np.all(err <= rtol * want + 1e-30), (d, mapping, sched, rho, float((err / np.maximum(want, 1e-30)).max()))
+        if ref is None:
+            ref = got
+        assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), (d, mapping, sched, rho)
+
+
 def test_edm_f32x2_matches_scalar():
     xh = synth.uniform_points(700, 64, 77)
     x = torch.from_numpy(xh).cuda()
