@@ -243,6 +243,11 @@ td_status td_collide_strict(const int32_t *centers, const int32_t *radii, uint32
  * and write aligned 16-byte chunks (distances) or whole 32-bit words (collision bits, one
  * __ballot_sync per word).  rho: 8, 16 or 32.  stats (host, may be NULL): the block counts of
  * the triangle of side n - 1.
+ * td_collide_strict_blocks also takes rho = 64: the 64 x 64 blocks of td_collide over the
+ * triangle of the n points (its kernel and predicate, issued by g(lambda) or BB, persistent),
+ * after clearing the bit array on `stream`; each block's nonzero 32-pair row pieces are ORed
+ * into the one or two words they straddle (atomically: pieces of neighbouring blocks share
+ * words).  The fast form when collisions are sparse; stats: the blocks of that triangle.
  * td_edm_strict_blocks: 1 <= d <= 8 (larger d: td_edm_strict); x and out 16-byte aligned.
  * td_collide_strict_blocks: centers, radii and bits 4-byte aligned.
  * n < 2: no-op.  Other errors as td_edm_strict / td_collide_strict. */

@@ -442,6 +442,28 @@ td_status td_collide_strict_blocks(td_mapping m, const int32_t *centers, const i
                                    uint32_t rho, uint32_t *bits, td_launch_stats *stats, void *stream)
 {
     g_err[0] = 0;
+    if (rho == 64) {  // td_collide's 64 x 64 blocks over the n-point triangle, bits ORed into a cleared array
+        if (m != TD_MAP_LTM && m != TD_MAP_BB)
+            return fail(TD_ERR_UNSUPPORTED, "the block-mapped strict forms serve LTM and BB");
+        const uint64_t nb = (uint64_t(n) + 63) / 64;
+        Plan q;
+        q.nb = static_cast<uint32_t>(nb);
+        q.blocks = m == TD_MAP_BB ? nb * nb : tri(nb);
+        q.useful = tri(nb);
+        q.launches = 1;
+        if (n < 2) {
+            fill_stats(stats, q, 0);
+            return TD_OK;
+        }
+        if (!centers || !radii || !bits) return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be non-NULL");
+        if ((reinterpret_cast<uintptr_t>(centers) | reinterpret_cast<uintptr_t>(radii) | reinterpret_cast<uintptr_t>(bits)) & 3u)
+            return fail(TD_ERR_INVALID_ARG, "centers, radii and bits must be 4-byte aligned");
+        uint64_t ctas = 0;
+        const td_status s64 = launch_collide_strict64(m, centers, radii, n, bits, td_collide_strict_words(n), q,
+                                                      static_cast<cudaStream_t>(stream), &ctas);
+        fill_stats(stats, q, ctas);
+        return s64;
+    }
     Plan p;
     td_status st = td::plan_strict_blocks(m, n, rho, p);
     if (st != TD_OK) return st;

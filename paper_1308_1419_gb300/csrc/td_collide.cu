@@ -46,16 +46,40 @@ __device__ __forceinline__ int4 load_sphere(const int32_t *__restrict__ c, const
 
 __device__ __forceinline__ float4 to_f4(const int4 &p) { return make_float4(float(p.x), float(p.y), float(p.z), float(p.w)); }
 
-// Lane r's word of tile (tr, tc) (row 32 tr + r) after the validity mask -- columns and rows
-// below n, j < i on the diagonal -- stored with the other lanes' words as 128 contiguous bytes.
-__device__ __forceinline__ void store_word(uint32_t word, uint32_t tr, uint32_t tc, uint32_t n, uint32_t lane,
-                                           uint32_t *__restrict__ table)
+// Lane r's word of tile (tr, tc) (row 32 tr + r) after the validity mask: columns and rows below
+// n, j < i on the diagonal.  Warp-collective.
+__device__ __forceinline__ uint32_t mask_word(uint32_t word, uint32_t tr, uint32_t tc, uint32_t n, uint32_t lane)
 {
     if (tr == tc || 32 * tr + 32 > n || 32 * tc + 32 > n) {
         const uint32_t colmask = __ballot_sync(0xffffffffu, 32 * tc + lane < n);
         word &= 32 * tr + lane < n ? (colmask & (tr == tc ? ((1u << lane) - 1u) : ~0u)) : 0u;
     }
-    table[(tri(tr) + tc) * 32 + lane] = word;
+    return word;
+}
+
+// The tile table: lane r's masked word stored with the other lanes' words as 128 contiguous bytes.
+__device__ __forceinline__ void store_word(uint32_t word, uint32_t tr, uint32_t tc, uint32_t n, uint32_t lane,
+                                           uint32_t *__restrict__ table)
+{
+    table[(tri(tr) + tc) * 32 + lane] = mask_word(word, tr, tc, n, lane);
+}
+
+// The strict bit array (pair (i, j), j < i, at bit i (i - 1) / 2 + j, LSB first; cleared before
+// the launch): lane r's masked word -- row i = 32 tr + r, columns 32 tc .. 32 tc + 31, so bits
+// k0 = i (i - 1) / 2 + 32 tc onwards -- is ORed into the one or two words it straddles, and only
+// if it has a bit set.  Every bit it holds is a real pair (j < i < n), so every word it touches
+// lies inside the array.
+__device__ __forceinline__ void or_strict(uint32_t word, uint32_t tr, uint32_t tc, uint32_t n, uint32_t lane,
+                                          uint32_t *__restrict__ bits)
+{
+    word = mask_word(word, tr, tc, n, lane);
+    if (word == 0) return;
+    const uint64_t i = 32 * uint64_t(tr) + lane;  // i >= 1: row 0 has no pair and an empty word
+    const uint64_t k0 = i * (i - 1) / 2 + 32 * uint64_t(tc);
+    const uint32_t sh = static_cast<uint32_t>(k0 & 31u);
+    uint32_t *w = bits + (k0 >> 5);
+    atomicOr(w, word << sh);
+    if (sh != 0 && (word >> (32 - sh)) != 0) atomicOr(w + 1, word >> (32 - sh));
 }
 
 // Exact pass of one tile: row spheres rows[0 .. 31] against this lane's column sphere q; returns
@@ -79,7 +103,9 @@ __device__ __noinline__ uint32_t exact_word(const int4 *rows, const int4 &q, boo
     return mine;
 }
 
-template <class Tiles, bool P>
+// kStrict: the strict bit array instead of the tile table (or_strict instead of store_word); the
+// predicate passes are the same code, so both outputs hold the same decisions.
+template <class Tiles, bool P, bool kStrict>
 __global__ void __launch_bounds__(32 * kWarps)
     k_collide(Tiles tiles, const int32_t *__restrict__ c, const int32_t *__restrict__ rad, uint32_t n,
               uint32_t *__restrict__ table)
@@ -147,24 +173,29 @@ __global__ void __launch_bounds__(32 * kWarps)
             // exact pass of a tile: large values, or a pair in the band
             if (ex0) mine0 = exact_word(rows[warp] + 32 * h, q0, in32, lane);
             if (ex1 && second) mine1 = exact_word(rows[warp] + 32 * h, q1, in32, lane);
-            store_word(mine0, tr, 2 * bj, n, lane, table);
-            if (second) store_word(mine1, tr, 2 * bj + 1, n, lane, table);
+            if (kStrict) {
+                or_strict(mine0, tr, 2 * bj, n, lane, table);
+                if (second) or_strict(mine1, tr, 2 * bj + 1, n, lane, table);
+            } else {
+                store_word(mine0, tr, 2 * bj, n, lane, table);
+                if (second) store_word(mine1, tr, 2 * bj + 1, n, lane, table);
+            }
         }
     }
 }
 
-template <class Tiles>
+template <class Tiles, bool kStrict = false>
 td_status launch(const Tiles &t, bool P, const int32_t *c, const int32_t *r, uint32_t n, uint32_t *table,
                  cudaStream_t st, uint64_t *ctas)
 {
     const uint64_t need = (t.units + kWarps - 1) / kWarps;
     if (P) {
-        auto k = k_collide<Tiles, true>;
+        auto k = k_collide<Tiles, true, kStrict>;
         const uint64_t g = persistent_ctas(reinterpret_cast<const void *>(k), 32 * kWarps, 0, need);
         k<<<dim3(static_cast<uint32_t>(g)), 32 * kWarps, 0, st>>>(t, c, r, n, table);
         *ctas += g;
     } else {
-        k_collide<Tiles, false><<<dim3(static_cast<uint32_t>(need)), 32 * kWarps, 0, st>>>(t, c, r, n, table);
+        k_collide<Tiles, false, kStrict><<<dim3(static_cast<uint32_t>(need)), 32 * kWarps, 0, st>>>(t, c, r, n, table);
         *ctas += need;
     }
     return launch_status("td_collide kernel");
@@ -181,6 +212,16 @@ td_status launch_collide(td_mapping m, td_schedule s, const int32_t *c, const in
     if (m == TD_MAP_UTM_BLOCK) return launch(tiles::UtmBlk{tri(nt), nt}, P, c, r, n, table, st, ctas);
     if (m == TD_MAP_BB) return launch(tiles::bb_source(p), P, c, r, n, table, st, ctas);
     return fail(TD_ERR_UNSUPPORTED, "td_collide supports LTM, BB and UTM-BLOCK");
+}
+
+td_status launch_collide_strict64(td_mapping m, const int32_t *c, const int32_t *r, uint32_t n, uint32_t *bits,
+                                  uint64_t words, const Plan &p, cudaStream_t st, uint64_t *ctas)
+{
+    td_status s = cuda_status(cudaMemsetAsync(bits, 0, words * 4, st), "strict collision bits clear");
+    if (s != TD_OK) return s;
+    if (m == TD_MAP_LTM) return launch<tiles::Ltm, true>(tiles::ltm_source(p), true, c, r, n, bits, st, ctas);
+    if (m == TD_MAP_BB) return launch<tiles::Bb, true>(tiles::bb_source(p), true, c, r, n, bits, st, ctas);
+    return fail(TD_ERR_UNSUPPORTED, "the strict collision bits by 64 x 64 blocks serve LTM and BB");
 }
 
 }  // namespace td

@@ -65,6 +65,11 @@ td_status launch_edm_chunked(td_mapping m, const float *x, uint32_t n, uint32_t 
 // planned for side n - 1.
 td_status launch_collide_chunked(td_mapping m, const int32_t *c, const int32_t *r, uint32_t n, uint32_t rho,
                                  uint32_t *bits, const Plan &p, cudaStream_t st, uint64_t *ctas);
+// Strict-lower collision bits (`words` of them) by the 64 x 64 blocks of td_collide over the
+// n-point triangle, p planned as for td_collide: the array is cleared, then each block's nonzero
+// row pieces are ORed in (LTM and BB).
+td_status launch_collide_strict64(td_mapping m, const int32_t *c, const int32_t *r, uint32_t n, uint32_t *bits,
+                                  uint64_t words, const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_pair(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,
                           float *out, const Plan &p, cudaStream_t st, uint64_t *ctas);
 td_status launch_edm_tiled(td_mapping m, td_schedule s, const float *x, uint32_t n, uint32_t d, uint32_t rho,

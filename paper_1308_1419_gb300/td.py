@@ -286,7 +286,8 @@ def td_edm_strict_blocks(mapping, x: torch.Tensor, rho: int, out: torch.Tensor =
 
 def td_collide_strict_blocks(mapping, centers: torch.Tensor, radii: torch.Tensor, rho: int = 32,
                              bits: torch.Tensor = None, stream=None):
-    """td_collide_strict's bits mapped at the block level (LTM or BB, rho 8/16/32), and stats."""
+    """td_collide_strict's bits mapped at the block level (LTM or BB, rho 8/16/32 strips, or 64:
+    td_collide's 64 x 64 blocks ORing the rare set bits into a cleared array), and stats."""
     n = radii.numel()
     cp = _dev(centers, torch.int32, 3 * n, "centers")
     rp = _dev(radii, torch.int32, n, "radii")

@@ -114,7 +114,7 @@ def test_edm_strict_blocks_large_sampled():
 
 
 @pytest.mark.parametrize("mapping", ["LTM", "BB"])
-@pytest.mark.parametrize("rho", [8, 16, 32])
+@pytest.mark.parametrize("rho", [8, 16, 32, 64])
 def test_collide_strict_blocks_matches_oracle(mapping, rho):
     for n, bits, rmax in [(2, 4, 8), (3, 4, 8), (33, 6, 20), (34, 6, 20), (100, 10, 64), (1000, 12, 256),
                           (3001, 14, 2048)]:
@@ -134,7 +134,7 @@ def test_collide_strict_blocks_exact_paths():
     r = np.tile(r, 40)
     small = c[:, :] % 1000
     for cc in (c, small.astype(np.int32)):
-        for rho in (8, 32):
+        for rho in (8, 32, 64):
             got, _ = td.td_collide_strict_blocks("LTM", torch.from_numpy(cc).cuda(), torch.from_numpy(r).cuda(), rho)
             words = td.td_collide_strict_words(len(r))
             assert np.array_equal(got[:words].cpu().numpy().view(np.uint32), oracle.collide_strict(cc, r)), rho
@@ -146,21 +146,42 @@ def test_collide_strict_blocks_workload():
     ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
     words = td.td_collide_strict_words(32768)
     ref = td.td_collide_strict(ct, rt)[:words]
-    for mapping, rho in (("LTM", 32), ("BB", 32), ("LTM", 16)):
+    for mapping, rho in (("LTM", 32), ("BB", 32), ("LTM", 16), ("LTM", 64), ("BB", 64)):
         got, _ = td.td_collide_strict_blocks(mapping, ct, rt, rho)
         assert torch.equal(got[:words], ref), (mapping, rho)
     assert np.array_equal(ref.cpu().numpy().view(np.uint32), oracle.collide_strict(c, r))
+
+
+def test_collide_strict_blocks64_dense():
+    """Every pair collides (all centres equal): with rho = 64 every word of the array is set by the
+    OR of the row pieces of neighbouring blocks, including the words shared across block and row
+    boundaries.  The array is cleared by the call: a buffer full of ones gives the same result."""
+    for n in (2, 31, 33, 64, 65, 1000, 3001):
+        c = np.zeros((n, 3), dtype=np.int32)
+        r = np.full(n, 5, dtype=np.int32)
+        ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+        words = td.td_collide_strict_words(n)
+        want = oracle.collide_strict(c, r)
+        for mapping in ("LTM", "BB"):
+            bits = torch.full((max(words, 4),), -1, dtype=torch.int32, device="cuda")
+            got, st = td.td_collide_strict_blocks(mapping, ct, rt, 64, bits)
+            assert np.array_equal(got[:words].cpu().numpy().view(np.uint32), want), (n, mapping)
+            nb = -(-n // 64)
+            assert st["useful_blocks"] == nb * (nb + 1) // 2
 
 
 def test_strict_blocks_errors_and_no_ops():
     x = torch.zeros(10, 3, device="cuda")
     c = torch.zeros(10, 3, dtype=torch.int32, device="cuda")
     r = torch.zeros(10, dtype=torch.int32, device="cuda")
-    for bad in (("UTM", 16), ("RB", 16), ("LTM", 64), ("LTM", 12)):
+    for bad in (("UTM", 16), ("RB", 16), ("LTM", 12), ("LTM", 128), ("UTM-BLOCK", 64)):
         with pytest.raises(td.TDError):
             td.td_edm_strict_blocks(bad[0], x, bad[1])
         with pytest.raises(td.TDError):
             td.td_collide_strict_blocks(bad[0], c, r, bad[1])
+    with pytest.raises(td.TDError):
+        td.td_edm_strict_blocks("LTM", x, 64)  # 64 x 64 blocks: the collision bits only
+    td.td_collide_strict_blocks("LTM", c[:1], r[:1], 64)
     with pytest.raises(td.TDError):
         td.td_edm_strict_blocks("LTM", torch.zeros(10, 9, device="cuda"), 16)  # d > 8: td_edm_strict
     td.td_edm_strict_blocks("LTM", torch.zeros(1, 3, device="cuda"), 16)
@@ -179,6 +200,6 @@ def test_collide_strict_blocks_random_shapes():
         words = td.td_collide_strict_words(n)
         ref = td.td_collide_strict(ct, rt)[:words].clone()
         for mapping in ("LTM", "BB"):
-            for rho in (8, 16, 32):
+            for rho in (8, 16, 32, 64):
                 got, _ = td.td_collide_strict_blocks(mapping, ct, rt, rho)
                 assert torch.equal(got[:words], ref), (n, bits_, mapping, rho)
