@@ -27,6 +27,10 @@
 // spheres lie in its domain (coordinates in [-2^30, 2^30), radii in [0, 2^14]), the 64/128-bit
 // form otherwise, so every int32 input is decided exactly.  Only diagonal and edge tiles apply the
 // validity mask (columns and rows below n, j < i on the diagonal).
+// The same kernel also writes the strict bit array of td_collide_strict (pair (i, j), j < i, at
+// bit i (i - 1) / 2 + j): the caller clears the array, and each masked row word that has a bit set
+// is ORed, atomically, into the one or two array words it straddles (row pieces of neighbouring
+// blocks share words).  With sparse collisions almost nothing is written.
 #include "td_collide.cuh"
 #include "td_internal.h"
 #include "td_tiles.cuh"
